@@ -1,0 +1,88 @@
+/* FP64 CPU oracle of the wave path tracer (test infrastructure only).
+ *
+ * Plain, slow, double-precision restatement of the method of
+ * "HoloPathTracer: Fast and Accurate Wave Path Tracing for Holography"
+ * (ACM TOG 45(4), 2026): the nine stages of Sec. 4, the wave-facet model of
+ * Sec. 4.1, the coherent/incoherent split and virtual image point of Sec. 4.2,
+ * the Path-Reuse accumulation of Eq. 5 (Sec. 4.3), the rendering equation
+ * (Eq. 1) for the incoherent amplitude and the Rayleigh-Sommerfeld integral
+ * (Eq. 2) as the estimator the per-pixel sum computes.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  It shares no code with the CUDA library.
+ */
+#ifndef HPT_ORACLE_H
+#define HPT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nv, nt, nm, ntex, nl, npts;
+    const float *verts;      /* [nv][3] metres                          */
+    const float *normals;    /* [nv][3] per-vertex shading normals      */
+    const float *uvs;        /* [nv][2]                                 */
+    const uint32_t *tris;    /* [nt][3]                                 */
+    const uint32_t *tri_mat; /* [nt]                                    */
+    const int32_t *mat_type; /* [nm] 0 lambert 1 ggx 2 mirror 3 dielectric 4 emitter */
+    const float *mat_albedo; /* [nm][3] */
+    const float *mat_rough;  /* [nm]    */
+    const float *mat_ior;    /* [nm]    */
+    const float *mat_Le;     /* [nm][3] */
+    const int32_t *mat_tex;  /* [nm]    */
+    const int32_t *mat_emit_tex; /* [nm] */
+    const int32_t *mat_light;    /* [nm] */
+    const float *tex_data;   /* texels, RGB row-major */
+    const int32_t *tex_info; /* [ntex][3] offset, w, h */
+    const float *lights;     /* [nl][12] corner, edge_u, edge_v, Le */
+    const double *points;    /* [npts][4] position, amplitude */
+    int32_t cache_res;
+    const float *cache_bmin, *cache_bmax; /* [3] */
+    const uint16_t *cache_E; /* [res][res][res][3] IEEE binary16 bits */
+} or_scene;
+
+typedef struct {
+    int32_t W, H;
+    double pitch;
+    int32_t n_lambda;
+    double lambda[3];
+    int32_t channel[3];
+    int32_t spp, max_depth, K, hologram_offset;
+    uint64_t seed, phase_seed;
+    int32_t phase_mode;      /* 0 hashed facet phase, 1 zero phase */
+    double facet_size;
+    double T[16];            /* world -> hologram, row-major, rigid */
+    int32_t use_cache;
+} or_render;
+
+/* per-sample debug record (or_sample) */
+enum { OR_REC_L, OR_REC_BETA, OR_REC_OPL, OR_REC_R, OR_REC_COS, OR_REC_COSP, OR_REC_VP,
+       OR_REC_PX, OR_REC_PY, OR_REC_PZ, OR_REC_TRI, OR_REC_FLAGS, OR_REC_RE, OR_REC_IM,
+       OR_REC_NRAYS, OR_REC_U0, OR_REC_N };
+
+void *or_build(const or_scene *s);
+void or_free(void *h);
+/* out: [n_lambda][K][n_pixels][2] complex128; flags (optional): [n_lambda][n_pixels]
+ * number of samples that met a near-edge or near-tie ray query. Returns 0 or <0. */
+int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixels,
+             double *out, int64_t *flags, int n_threads);
+int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double *rec);
+
+/* building blocks exposed for the pins */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void or_cone_dir(double lambda, double pitch, double u0, double u1, double d[3], double *pdf);
+int or_closest_hit(void *h, const double o[3], const double d[3], double tmin, double tmax,
+                   int brute, double *t, int32_t *tri);
+double or_fresnel_dielectric(double cos_i, double n_i, double n_t);
+void or_ggx_eval(double alpha, double F0, const double wo[3], const double wi[3], double *f, double *pdf);
+int or_ggx_sample(double alpha, double F0, const double wo[3], double u0, double u1,
+                  double wi[3], double *weight, double *pdf);
+void or_frame(const double n[3], double t[3], double b[3]);
+double or_half_to_double(uint16_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
