@@ -1,0 +1,300 @@
+"""Benchmark of the wave path tracer on the headline workload.
+
+Workload: the 30-icosphere scene (~24k triangles, Lambertian / GGX / mirror / dielectric, one
+area light), 1920x1080 SLM at 6.4 um, RGB (638/520/450 nm), 64 spp, depth 4, K = 8
+Path-Reuse holograms: 398 M path samples per step.  One step = one full hologram set.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = path samples / s over the whole job (all ranks); the plain
+form (FP64 coherent arithmetic, one launch per wavelength) is timed beside the mixed-precision
+batched form (double-float coherent arithmetic, all wavelengths and holograms in one launch).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "path samples/s & 1080p RGB K=8 holograms/s vs plain FP64 form; p50/p99 latency"
+UNIT = "path samples/s"
+# FP32 ALU peak of a GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA
+# x 2.07 GHz (maximum SM clock).
+SM_COUNT, FP32_LANES, SM_MHZ_MAX = 152, 128, 2070.0
+ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
+# algorithmic FP32 work per counted event (see the design notes): two child-box slab tests per
+# node visit are counted as two box tests
+FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(scene, r, n_pixels, seed=5):
+    """The FP64 oracle as it stands, on all host cores, over a seeded pixel sample."""
+    import oracle
+    o = oracle.Oracle(scene)
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(r.W * r.H, n_pixels, replace=False)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o.trace(r, pix, n_threads=cores)
+    dt = time.perf_counter() - t0
+    samples = n_pixels * len(r.lambdas) * r.spp
+    return samples / dt, dt, cores, samples
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, steps = bounded pixel samples."""
+    from paper_2606_14173_gb300 import scenes as S
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = S.config1_scene()
+    r = S.config2_render()
+    n_pix = 2048
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sc, r, 256)
+    rates, dts, samples = [], [], 0
+    for k in range(args.steps):
+        rate, dt, cores, ns = cpu_oracle_rate(sc, r, n_pix, seed=100 + k)
+        dts.append(dt)
+        samples += ns
+    total = sum(dts)
+    value = samples / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg2: 30-icosphere scene (~24k tris), 1920x1080 SLM 6.4 um, RGB, 64 spp, "
+                                   "depth 4, K=8", "sample": f"{n_pix} random pixels x 3 wavelengths x 64 spp per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n_pix} seeded random pixels of the 1080p frame per step, all 3 wavelengths, "
+                                       f"64 spp, K=8"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2606_14173_gb300 import build as pbuild, hpt, scenes as S
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        pbuild.build()
+    barrier(world)
+    ctx = hpt.Context(local)
+    sc = S.config1_scene()
+    sid = ctx.upload_scene(sc)
+    r = S.config2_render(seed=1 + rank)
+    samples_per_step = r.path_samples()
+    out = hpt.alloc_output(r)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step_mixed():
+        ctx.trace(sid, r, out, precision=hpt.PREC_DF32, stream=stream)
+
+    r_plain = [S.config2_render(seed=1 + rank, lambdas=(l,), channels=(c,)) for l, c in zip(r.lambdas, r.channels)]
+    outs_plain = [hpt.alloc_output(rp) for rp in r_plain]
+
+    def step_plain():
+        for rp, op in zip(r_plain, outs_plain):
+            ctx.trace(sid, rp, op, precision=hpt.PREC_FP64, stream=stream)
+
+    def timed(step, k, w, sample_clocks=False):
+        for _ in range(w):
+            step()
+        ctx.sync()
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        if sample_clocks:
+            clk.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(k):
+            flush.zero_()
+            ev[2 * i].record(stream)
+            step()
+            ev[2 * i + 1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = clk.stop() if sample_clocks else None
+        ctx.sync()
+        total_ms = t0.elapsed_time(t1)
+        launch_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(k)]
+        return allreduce_max(total_ms, world), launch_ms, clocks
+
+    total_ms, launch_ms, clocks = timed(step_mixed, args.steps, args.warmup, sample_clocks=True)
+    value = world * samples_per_step * args.steps / (total_ms / 1e3)
+    holo_per_s = world * r.K * args.steps / (total_ms / 1e3)
+
+    plain = None
+    if not args.no_plain:
+        pm, plm, _ = timed(step_plain, max(2, args.steps // 2), 1)
+        kp = max(2, args.steps // 2)
+        plain = {"value": world * samples_per_step * kp / (pm / 1e3), "unit": UNIT,
+                 "holograms_per_s": world * r.K * kp / (pm / 1e3), "ms_per_step": pm / kp,
+                 "form": "FP64 coherent arithmetic, one launch per wavelength (3 per step), K=8 path reuse"}
+
+    # end to end through the public API with host memory: result copied to pinned host memory
+    host = torch.empty(tuple(out.shape), dtype=torch.complex64, pin_memory=True).numpy()
+    for _ in range(max(1, args.warmup)):
+        ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
+    barrier(world)
+    t0 = time.perf_counter()
+    k_e2e = max(2, args.steps // 2)
+    for _ in range(k_e2e):
+        ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    import ctypes
+    h2d = ctypes.sizeof(hpt.RenderDesc) + 16 + 8 * 0   # render descriptor marshalled per call
+    e2e = {"value": world * samples_per_step * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(host.nbytes),
+           "api": "hpt_trace_host (device trace + D2H copy of all K x 3 fields into pinned host memory)"}
+
+    # roofline of the trace kernel: algorithmic FP32 work from the per-sample work counters
+    cnt = ctx.trace_counters(sid, r, out, precision=hpt.PREC_DF32)
+    ns = max(cnt["samples"], 1)
+    vertices = cnt["shadow_rays"] + cnt["bounces"] + cnt["refines"]
+    flops = (cnt["box_tests"] * FLOP_PER["box_tests"] + cnt["tri_tests"] * FLOP_PER["tri_tests"]
+             + cnt["refines"] * FLOP_PER["refines"] + vertices * FLOP_PER["vertex"]
+             + ns * r.K * FLOP_PER["hologram"])
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = flops / avg_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "per_sample": {k: v / ns for k, v in cnt.items() if k != "samples"},
+                "flops_per_sample": flops / ns}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, cores, nsamp = cpu_oracle_rate(sc, r, 8192)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"8192 seeded random pixels of the 1080p frame x 3 wavelengths x 64 spp "
+                         f"({nsamp} path samples, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+                "config": {"workload": "cfg2: 30-icosphere scene (~24k tris, Lambert/GGX/mirror/dielectric, 1 area "
+                                       "light), 1920x1080 SLM 6.4 um, RGB 638/520/450 nm, 64 spp, depth 4, K=8",
+                           "path_samples_per_step": samples_per_step, "parallelism": f"replicas x{world}",
+                           "l2": "flushed between steps (256 MiB write)"},
+                "holograms_per_s": holo_per_s, "plain_fp64": plain, "launch_ms": launch_ms,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

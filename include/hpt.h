@@ -1,0 +1,201 @@
+/* hpt.h -- C-ABI of the GB300 wave path tracer.
+ *
+ * The library computes, for every pixel of a spatial light modulator (SLM) and
+ * every wavelength, K complex fields U_m (m = 0..K-1) by Monte Carlo wave path
+ * tracing, following "HoloPathTracer: Fast and Accurate Wave Path Tracing for
+ * Holography" (ACM TOG 45(4), 2026):
+ *
+ *   - Sec. 4 (nine stages s1-s9): a ray leaves the pixel centre in a random
+ *     direction inside the SLM diffraction cone theta <= asin(lambda / 2p)
+ *     (Sec. 4.1), is mapped to world space by T^-1 (Eq. 3), follows delta
+ *     (mirror / smooth dielectric) lobes coherently while accumulating the
+ *     optical path length OPL = sum n_i L_i (Sec. 4.2) and stops at the first
+ *     non-delta hit, the real image point P;
+ *   - the amplitude at P is sqrt(L), L estimated by incoherent path tracing of
+ *     the rendering equation (Eq. 1) with next-event estimation, and, past the
+ *     first bounce, optionally read from an ambient radiance cache (Sec. 4.2);
+ *   - the virtual image point P' = O + d_OPL v is mapped back by Q = T P' and
+ *     its contribution (1/(i lambda)) sqrt(L) cos(theta) / (r pdf_A)
+ *     * exp(i (2 pi r / lambda + phi_m)) is summed into U_m, the Monte Carlo
+ *     estimate of the Rayleigh-Sommerfeld integral (Eq. 2);
+ *   - Path Reuse (Eq. 5, Sec. 4.3): all K holograms share one path set and
+ *     differ only in the random facet phase phi_m.
+ *
+ * Conventions for every entry point:
+ *   - units are SI metres; all arrays are row-major and tightly packed;
+ *   - host pointers are only read during the call; the library copies what it
+ *     keeps; device pointers (out_dev) are owned by the caller;
+ *   - calls return HPT_OK (0) or a negative status, never throw, and leave a
+ *     message for hpt_last_error();
+ *   - one context serves one CUDA device; calls on one context may come from
+ *     several host threads (they are serialised internally).
+ */
+#ifndef HPT_H
+#define HPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hpt_status;
+enum {
+    HPT_OK = 0,
+    HPT_ERR_INVALID_ARG = -1,   /* bad pointer, size, NaN/Inf input, out-of-range index   */
+    HPT_ERR_OOM = -2,           /* device allocation failed or budget exceeded            */
+    HPT_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the cause)     */
+    HPT_ERR_TIMEOUT = -4,       /* hpt_wait ran out of time                               */
+    HPT_ERR_BUSY = -5,          /* serving queue full / admission refused                 */
+    HPT_ERR_NOT_FOUND = -6,     /* unknown scene or request id                            */
+    HPT_ERR_UNSUPPORTED = -7,   /* valid request outside what this build supports         */
+    HPT_ERR_DEVICE = -8         /* the kernel reported an internal error (status word)    */
+};
+
+/* material kinds (Sec. 4.2: mirror and dielectric are delta lobes, the rest non-delta) */
+enum { HPT_LAMBERT = 0, HPT_GGX = 1, HPT_MIRROR = 2, HPT_DIELECTRIC = 3, HPT_EMITTER = 4 };
+enum { HPT_PHASE_HASH = 0, HPT_PHASE_ZERO = 1 };
+/* arithmetic of the coherent chain (ray origin/direction, hit distance, OPL, phase):
+ * FP64 = native double; DF32 = double-float (unevaluated sum of two floats, ~48-bit mantissa) */
+enum { HPT_PREC_FP64 = 0, HPT_PREC_DF32 = 1 };
+
+typedef struct hpt_ctx hpt_ctx;
+
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* serving admission limit for in-flight outputs; 0 = free HBM */
+    int32_t max_inflight;       /* serving: requests on the device at once (0 -> 8)           */
+    int32_t flags;              /* reserved, 0                                                 */
+} hpt_ctx_desc;
+
+/* Scene description.  All arrays are host memory, read during hpt_scene_upload only.
+ *  verts    float[nv][3]   vertex positions (float32 values; the geometry is exactly these)
+ *  normals  float[nv][3]   per-vertex shading normals (interpolated, renormalised)
+ *  uvs      float[nv][2]   texture coordinates
+ *  tris     uint32[nt][3]  vertex indices; winding gives the geometric normal (e1 x e2)
+ *  tri_mat  uint32[nt]     material index
+ *  materials: kind, albedo (mirror reflectance / GGX F0 / Lambert albedo), GGX roughness
+ *    (alpha = roughness^2), index of refraction, emitted radiance Le (one-sided, toward the
+ *    winding normal), albedo texture id (-1 none), emit_tex (Le scaled by the texture),
+ *    light (rectangular light this EMITTER surface belongs to, -1 none)
+ *  textures: float RGB texels, row-major, tex_info[i] = {offset in floats, width, height};
+ *    sampled bilinearly with clamp-to-edge, texel centres at (i + 1/2) / width
+ *  lights   float[nl][12]  rectangular lights for next-event estimation:
+ *    corner, edge_u, edge_v, Le; they emit toward edge_u x edge_v
+ *  points   double[np][4]  deterministic point emitters (position, amplitude a); each adds
+ *    a exp(i k r) cos(theta) / r to every hologram of the pixels whose cone contains it
+ *  cache    optional ambient radiance cache: res^3 cells over [bmin, bmax], binary16 RGB
+ *    irradiance at cell centres, layout [z][y][x][c], read trilinearly                      */
+typedef struct {
+    int32_t kind;
+    float albedo[3];
+    float roughness;
+    float ior;
+    float Le[3];
+    int32_t tex;
+    int32_t emit_tex;
+    int32_t light;
+} hpt_material;
+
+typedef struct {
+    int32_t nv, nt, nm, ntex, nl, np;
+    const float *verts;
+    const float *normals;
+    const float *uvs;
+    const uint32_t *tris;
+    const uint32_t *tri_mat;
+    const hpt_material *materials;
+    const float *tex_data;
+    int64_t tex_floats;
+    const int32_t *tex_info;
+    const float *lights;
+    const double *points;
+    int32_t cache_res;
+    float cache_bmin[3], cache_bmax[3];
+    const uint16_t *cache_E;
+} hpt_scene_desc;
+
+/* Render description (one hologram set).
+ *  W, H, pitch   SLM size in pixels and pixel pitch (m); pixel (i, j) centre is
+ *                ((i + 1/2 - W/2) p, (j + 1/2 - H/2) p, 0) in hologram space, normal +z
+ *  lambda[c]     wavelengths (m), n_lambda <= 3; channel[c] = RGB channel of the scene read
+ *  spp           coherent samples per pixel and wavelength (N)
+ *  max_depth     scattering vertices per path (delta vertices included); >= 1
+ *  K             holograms from one path set (Path Reuse), 1..8; hologram_offset shifts m
+ *  seed          key of the path draws; phase_seed key of the facet phases
+ *  phase_mode    HPT_PHASE_HASH: phi_m uniform in [0, 2 pi) per facet cell (edge
+ *                facet_size, world space) and hologram; HPT_PHASE_ZERO: phi_m = 0
+ *  T             world -> hologram transform, row-major 4x4, must be rigid
+ *  precision     HPT_PREC_FP64 or HPT_PREC_DF32 (coherent chain arithmetic)
+ *  use_cache     read the scene's ambient cache past the first incoherent bounce          */
+typedef struct {
+    int32_t W, H;
+    double pitch;
+    int32_t n_lambda;
+    double lambda[3];
+    int32_t channel[3];
+    int32_t spp, max_depth, K, hologram_offset;
+    uint64_t seed, phase_seed;
+    int32_t phase_mode;
+    double facet_size;
+    double T[16];
+    int32_t precision;
+    int32_t use_cache;
+} hpt_render_desc;
+
+/* Output layout of every trace: complex64 (float re, float im) [n_lambda][K][H][W];
+ * out_bytes must be >= 8 * n_lambda * K * H * W. */
+
+/* Create a context on CUDA device 'device'. desc may be NULL (defaults). */
+hpt_status hpt_create(hpt_ctx **ctx, int device, const hpt_ctx_desc *desc);
+/* Finish all work, free every device allocation of the context. ctx may be NULL. */
+void hpt_destroy(hpt_ctx *ctx);
+/* Message of the last failing call on this thread ("" if none). Valid until the next call. */
+const char *hpt_last_error(void);
+
+/* Copy a scene to the device, build its BVH; *scene_id receives a handle. Synchronous. */
+hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *scene, uint64_t *scene_id);
+/* Free a scene after all work using it has finished. */
+hpt_status hpt_scene_release(hpt_ctx *ctx, uint64_t scene_id);
+/* Bytes of device memory the scene occupies (BVH, triangles, attributes, textures, cache). */
+hpt_status hpt_scene_info(hpt_ctx *ctx, uint64_t scene_id, uint64_t *device_bytes,
+                          int32_t *n_nodes, int32_t *bvh_depth);
+
+/* Trace one render description into the caller's device buffer, asynchronously on
+ * 'cuda_stream' (a cudaStream_t, NULL = legacy default stream).  All wavelengths and all K
+ * holograms are produced by one persistent kernel launch. */
+hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                     void *out_dev, size_t out_bytes, void *cuda_stream);
+/* Same, end to end with host memory: the result is copied into out_host (pinned or pageable)
+ * before the call returns.  Uses a device buffer owned by the context. */
+hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                          void *out_host, size_t out_bytes, void *cuda_stream);
+/* Block until all work queued by this context has finished; then report (and clear) the
+ * kernel status word: HPT_OK, or HPT_ERR_DEVICE with the cause in hpt_last_error(). */
+hpt_status hpt_sync(hpt_ctx *ctx);
+
+/* Per-path-sample work counters of one trace (synchronous; for roofline accounting).
+ * counters[0..HPT_NCOUNTERS-1]: path samples, rays, box tests, triangle tests,
+ * coherent refinements, FP64 fallback traversals, NEE shadow rays, BSDF bounces. */
+enum { HPT_NCOUNTERS = 8 };
+hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                              void *out_dev, size_t out_bytes, uint64_t counters[HPT_NCOUNTERS]);
+
+/* ---- serving: continuous batching of render requests ---------------------------------- */
+/* Queue a request; the scheduler thread admits it when a slot and memory are free and runs
+ * it concurrently with the requests already on the device.  out_dev is caller-owned and must
+ * stay valid until the request completes. */
+hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                      void *out_dev, size_t out_bytes, uint64_t *req_id);
+/* *done = 1 when the request finished (its output is complete). */
+hpt_status hpt_poll(hpt_ctx *ctx, uint64_t req_id, int *done);
+/* Wait up to timeout_ms (0 = forever) for the request; HPT_ERR_TIMEOUT if not done. */
+hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_ms);
+/* Timestamps of a finished request in microseconds since the context was created:
+ * t[0] submitted, t[1] admitted (launched), t[2] completed. */
+hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

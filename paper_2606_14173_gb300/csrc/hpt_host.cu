@@ -1,0 +1,874 @@
+// Host runtime of the wave path tracer: contexts, scene upload with a binned-SAH BVH build,
+// render validation, launch slots, and the C-ABI entry points declared in include/hpt.h.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hpt.h"
+#include "hpt_internal.h"
+
+namespace hpt {
+int trace_blocks_per_sm(int prec, bool stats);
+cudaError_t launch_trace(int prec, bool stats, const JobTable *d_table, SlotScratch *d_scratch, int grid,
+                         cudaStream_t s);
+}  // namespace hpt
+
+using namespace hpt;
+
+// ------------------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static hpt_status fail(hpt_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? HPT_ERR_OOM : HPT_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+static RC make_rc(double x)
+{
+    RC r;
+    r.d = x;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+// ------------------------------------------------------------------------- BVH builder
+namespace {
+
+struct Box {
+    float lo[3], hi[3];
+    void reset()
+    {
+        for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    }
+    void grow(const Box &b)
+    {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], b.lo[k]); hi[k] = std::max(hi[k], b.hi[k]); }
+    }
+    void grow(const float *p)
+    {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
+    }
+    double area() const
+    {
+        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        if (dx < 0 || dy < 0 || dz < 0) return 0.0;
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct BuildNode {
+    Box box;
+    int left = -1, right = -1;   // build-node indices (inner)
+    int start = 0, count = 0;    // leaf range in the primitive order
+};
+
+struct Builder {
+    const std::vector<Box> &pb;
+    const std::vector<float> &cent;   // 3 per primitive
+    std::vector<int> idx;
+    std::vector<BuildNode> nodes;
+    int max_depth_seen = 0;
+    static constexpr int BINS = 32, LEAF_MAX = 4, DEPTH_LIMIT = 56;
+
+    Builder(const std::vector<Box> &pb_, const std::vector<float> &c_, std::vector<int> prims)
+        : pb(pb_), cent(c_), idx(std::move(prims)) {}
+
+    int make_leaf(const Box &b, int start, int count)
+    {
+        BuildNode n;
+        n.box = b;
+        n.start = start;
+        n.count = count;
+        nodes.push_back(n);
+        return (int)nodes.size() - 1;
+    }
+
+    int build(int start, int count, int depth)
+    {
+        max_depth_seen = std::max(max_depth_seen, depth);
+        Box b, cb;
+        b.reset();
+        cb.reset();
+        for (int i = start; i < start + count; ++i) {
+            b.grow(pb[idx[i]]);
+            cb.grow(&cent[3 * idx[i]]);
+        }
+        if (count <= LEAF_MAX || (depth >= DEPTH_LIMIT && count <= 255)) return make_leaf(b, start, count);
+        // binned SAH over the three axes
+        double best_cost = INFINITY;
+        int best_axis = -1, best_split = -1;
+        for (int ax = 0; ax < 3; ++ax) {
+            float ext = cb.hi[ax] - cb.lo[ax];
+            if (!(ext > 0.0f)) continue;
+            Box bb[BINS];
+            int bc[BINS] = {0};
+            for (int k = 0; k < BINS; ++k) bb[k].reset();
+            double scale = BINS / (double)ext;
+            for (int i = start; i < start + count; ++i) {
+                int k = std::min(BINS - 1, (int)((cent[3 * idx[i] + ax] - cb.lo[ax]) * scale));
+                bc[k]++;
+                bb[k].grow(pb[idx[i]]);
+            }
+            double la[BINS];
+            int ln[BINS];
+            Box acc;
+            acc.reset();
+            int n = 0;
+            for (int k = 0; k < BINS - 1; ++k) {
+                acc.grow(bb[k]);
+                n += bc[k];
+                la[k] = acc.area();
+                ln[k] = n;
+            }
+            acc.reset();
+            n = 0;
+            for (int k = BINS - 1; k > 0; --k) {
+                acc.grow(bb[k]);
+                n += bc[k];
+                if (ln[k - 1] == 0 || n == 0) continue;
+                double cost = la[k - 1] * ln[k - 1] + acc.area() * n;
+                if (cost < best_cost) { best_cost = cost; best_axis = ax; best_split = k; }
+            }
+        }
+        double leaf_cost = b.area() * count;
+        if (depth < DEPTH_LIMIT && count <= 255 && (best_axis < 0 || (best_cost >= leaf_cost && count <= 8)))
+            return make_leaf(b, start, count);
+        if (depth >= DEPTH_LIMIT) best_axis = -1;   // forced median split of an oversized deep node
+        int mid;
+        if (best_axis >= 0) {
+            double scale = BINS / (double)(cb.hi[best_axis] - cb.lo[best_axis]);
+            float lo = cb.lo[best_axis];
+            int ax = best_axis, sp = best_split;
+            auto it = std::partition(idx.begin() + start, idx.begin() + start + count, [&](int p) {
+                int k = std::min(BINS - 1, (int)((cent[3 * p + ax] - lo) * scale));
+                return k < sp;
+            });
+            mid = (int)(it - idx.begin());
+            if (mid == start || mid == start + count) mid = start + count / 2;
+        } else {
+            mid = start + count / 2;   // identical centroids: split the list
+        }
+        int id = (int)nodes.size();
+        nodes.push_back(BuildNode());
+        nodes[id].box = b;
+        int l = build(start, mid - start, depth + 1);
+        int r = build(mid, start + count - mid, depth + 1);
+        nodes[id].left = l;
+        nodes[id].right = r;
+        return id;
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ context
+struct SceneRec {
+    void *arena = nullptr;
+    size_t bytes = 0;
+    DevScene dev{};
+    int n_nodes = 0, depth = 0;
+    std::atomic<int> users{0};
+};
+
+struct Slot {
+    JobTable *d_table = nullptr;
+    SlotScratch *d_scratch = nullptr;
+    JobTable *h_table = nullptr;   // pinned
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+struct Request {
+    uint64_t id;
+    uint64_t scene;
+    DevJob job;         // with out pointer
+    int prec;
+    long long n_items;  // items of the whole request
+    long long next = 0; // next item to schedule
+    int steps_in_flight = 0;
+    size_t out_bytes;
+    double t_submit = 0, t_admit = -1, t_done = -1;
+    bool done = false;
+    hpt_status err = HPT_OK;
+};
+
+struct hpt_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int bps[2] = {1, 1};
+    std::mutex mu;
+    std::map<uint64_t, std::unique_ptr<SceneRec>> scenes;
+    uint64_t next_scene = 1;
+    static constexpr int NSLOTS = 16;
+    Slot slots[NSLOTS];
+    int next_slot = 0;
+    void *host_out_dev = nullptr;
+    float4 *d_sincos = nullptr;
+    size_t host_out_bytes = 0;
+    std::chrono::steady_clock::time_point t0;
+    // serving
+    uint64_t budget = 0;
+    int max_inflight = 8;
+    std::mutex smu;
+    std::condition_variable scv, dcv;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::vector<std::shared_ptr<Request>> active;
+    std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    uint64_t next_req = 1;
+    uint64_t bytes_active = 0;
+    bool stop = false;
+    std::thread sched;
+    cudaStream_t sstream = nullptr;
+    double now_us() const
+    {
+        return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+static hpt_status check_ctx(hpt_ctx *ctx)
+{
+    if (!ctx) return fail(HPT_ERR_INVALID_ARG, "ctx is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(HPT_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return HPT_OK;
+}
+
+static void sched_loop(hpt_ctx *ctx);
+
+extern "C" const char *hpt_last_error(void) { return g_err.c_str(); }
+
+extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *desc)
+{
+    g_err.clear();
+    if (!out) return fail(HPT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(HPT_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    auto ctx = std::make_unique<hpt_ctx>();
+    ctx->device = device;
+    ctx->t0 = std::chrono::steady_clock::now();
+    CUDA_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+    ctx->bps[0] = trace_blocks_per_sm(0, false);
+    ctx->bps[1] = trace_blocks_per_sm(1, false);
+    // cos/sin(2 pi k / 256) split into float pairs for the double-float cone sampler
+    float4 tab[256];
+    for (int k = 0; k < 256; ++k) {
+        double a = 2.0 * M_PI * k / 256.0;
+        double c = cos(a), s = sin(a);
+        float ch = (float)c, sh = (float)s;
+        tab[k] = make_float4(ch, (float)(c - ch), sh, (float)(s - sh));
+    }
+    CUDA_TRY(cudaMalloc(&ctx->d_sincos, sizeof tab));
+    CUDA_TRY(cudaMemcpy(ctx->d_sincos, tab, sizeof tab, cudaMemcpyHostToDevice));
+    for (int i = 0; i < hpt_ctx::NSLOTS; ++i) {
+        Slot &s = ctx->slots[i];
+        CUDA_TRY(cudaMalloc(&s.d_table, sizeof(JobTable)));
+        CUDA_TRY(cudaMalloc(&s.d_scratch, sizeof(SlotScratch)));
+        CUDA_TRY(cudaMemset(s.d_scratch, 0, sizeof(SlotScratch)));
+        CUDA_TRY(cudaMallocHost(&s.h_table, sizeof(JobTable)));
+        CUDA_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    }
+    if (desc) {
+        ctx->budget = desc->hbm_budget_bytes;
+        if (desc->max_inflight > 0) ctx->max_inflight = desc->max_inflight;
+    }
+    if (ctx->budget == 0) {
+        size_t fr = 0, tot = 0;
+        CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        ctx->budget = (uint64_t)(fr * 0.6);
+    }
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking));
+    hpt_ctx *raw = ctx.release();
+    raw->sched = std::thread(sched_loop, raw);
+    *out = raw;
+    return HPT_OK;
+}
+
+extern "C" void hpt_destroy(hpt_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->stop = true;
+    }
+    ctx->scv.notify_all();
+    if (ctx->sched.joinable()) ctx->sched.join();
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
+    for (auto &s : ctx->slots) {
+        cudaFree(s.d_table);
+        cudaFree(s.d_scratch);
+        cudaFreeHost(s.h_table);
+        cudaEventDestroy(s.done);
+    }
+    if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
+    if (ctx->d_sincos) cudaFree(ctx->d_sincos);
+    if (ctx->sstream) cudaStreamDestroy(ctx->sstream);
+    delete ctx;
+}
+
+// ------------------------------------------------------------------------ scene upload
+static bool finite3(const float *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, uint64_t *scene_id)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!d || !scene_id) return fail(HPT_ERR_INVALID_ARG, "scene or scene_id is NULL");
+    if (d->nv <= 0 || d->nt <= 0 || d->nm <= 0 || d->ntex < 0 || d->nl < 0 || d->np < 0)
+        return fail(HPT_ERR_INVALID_ARG, "bad counts nv=%d nt=%d nm=%d", d->nv, d->nt, d->nm);
+    if (!d->verts || !d->normals || !d->uvs || !d->tris || !d->tri_mat || !d->materials)
+        return fail(HPT_ERR_INVALID_ARG, "missing geometry array");
+    if (d->nt >= (1 << 23)) return fail(HPT_ERR_UNSUPPORTED, "more than 2^23 triangles");
+    for (int i = 0; i < d->nv; ++i) {
+        if (!finite3(d->verts + 3 * i) || !finite3(d->normals + 3 * i) || !std::isfinite(d->uvs[2 * i]) ||
+            !std::isfinite(d->uvs[2 * i + 1]))
+            return fail(HPT_ERR_INVALID_ARG, "non-finite vertex data at vertex %d", i);
+    }
+    for (int t = 0; t < d->nt; ++t) {
+        for (int k = 0; k < 3; ++k)
+            if (d->tris[3 * t + k] >= (uint32_t)d->nv) return fail(HPT_ERR_INVALID_ARG, "triangle %d index out of range", t);
+        if (d->tri_mat[t] >= (uint32_t)d->nm) return fail(HPT_ERR_INVALID_ARG, "triangle %d material out of range", t);
+    }
+    for (int m = 0; m < d->nm; ++m) {
+        const hpt_material &M = d->materials[m];
+        if (M.kind < 0 || M.kind > 4) return fail(HPT_ERR_INVALID_ARG, "material %d: bad kind %d", m, M.kind);
+        if (M.tex >= d->ntex) return fail(HPT_ERR_INVALID_ARG, "material %d: texture %d out of range", m, M.tex);
+        if (M.light >= d->nl) return fail(HPT_ERR_INVALID_ARG, "material %d: light %d out of range", m, M.light);
+        if (!finite3(M.albedo) || !finite3(M.Le) || !std::isfinite(M.roughness) || !std::isfinite(M.ior))
+            return fail(HPT_ERR_INVALID_ARG, "material %d: non-finite value", m);
+        if (M.kind == HPT_GGX && !(M.roughness > 0.0f)) return fail(HPT_ERR_INVALID_ARG, "material %d: GGX roughness must be > 0", m);
+        if (M.kind == HPT_DIELECTRIC && !(M.ior > 0.0f)) return fail(HPT_ERR_INVALID_ARG, "material %d: ior must be > 0", m);
+    }
+    for (int i = 0; i < d->ntex; ++i) {
+        const int32_t *ti = d->tex_info + 3 * i;
+        if (ti[0] < 0 || ti[1] <= 0 || ti[2] <= 0 || (int64_t)ti[0] + (int64_t)ti[1] * ti[2] * 3 > d->tex_floats)
+            return fail(HPT_ERR_INVALID_ARG, "texture %d out of bounds", i);
+    }
+    if (d->nl > 0 && !d->lights) return fail(HPT_ERR_INVALID_ARG, "lights is NULL");
+    if (d->np > 0 && !d->points) return fail(HPT_ERR_INVALID_ARG, "points is NULL");
+    if (d->cache_res < 0 || (d->cache_res > 0 && !d->cache_E)) return fail(HPT_ERR_INVALID_ARG, "bad cache");
+
+    const int nt = d->nt, nv = d->nv;
+    // primitive boxes and centroids; degenerate triangles never intersect and are left out
+    std::vector<Box> pb(nt);
+    std::vector<float> cent(3 * nt);
+    std::vector<int> prims;
+    prims.reserve(nt);
+    float max_abs = 0.0f;
+    for (int t = 0; t < nt; ++t) {
+        const float *p[3] = {d->verts + 3 * d->tris[3 * t], d->verts + 3 * d->tris[3 * t + 1],
+                             d->verts + 3 * d->tris[3 * t + 2]};
+        pb[t].reset();
+        for (int k = 0; k < 3; ++k) {
+            pb[t].grow(p[k]);
+            for (int c = 0; c < 3; ++c) max_abs = std::max(max_abs, std::fabs(p[k][c]));
+        }
+        for (int c = 0; c < 3; ++c) cent[3 * t + c] = (p[0][c] + p[1][c] + p[2][c]) / 3.0f;
+        double e1[3], e2[3];
+        for (int c = 0; c < 3; ++c) { e1[c] = (double)p[1][c] - p[0][c]; e2[c] = (double)p[2][c] - p[0][c]; }
+        double n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2], n2 = e1[0] * e2[1] - e1[1] * e2[0];
+        if (n0 * n0 + n1 * n1 + n2 * n2 > 0.0) prims.push_back(t);
+    }
+    if (prims.empty()) return fail(HPT_ERR_INVALID_ARG, "all triangles are degenerate");
+    Builder B(pb, cent, prims);
+    int root = B.build(0, (int)B.idx.size(), 0);
+    // flatten: kernel nodes hold both child boxes; leaves are encoded in the parent's link
+    const float pad = 2e-6f * max_abs + 1e-12f;
+    std::vector<float4> knodes;
+    std::vector<int> order;   // triangle ids in leaf order
+    order.reserve(B.idx.size());
+    std::vector<std::pair<int, int>> todo;   // (build node, kernel node slot)
+    auto emit_leaf_link = [&](const BuildNode &n) {
+        int start = (int)order.size();
+        for (int i = n.start; i < n.start + n.count; ++i) order.push_back(B.idx[i]);
+        return ~((start << 8) | n.count);
+    };
+    auto box_of = [&](const BuildNode *n, float lo[3], float hi[3]) {
+        for (int k = 0; k < 3; ++k) {
+            if (n) {
+                lo[k] = n->box.lo[k] - pad;
+                hi[k] = n->box.hi[k] + pad;
+            } else {
+                lo[k] = 1e30f;   // far-away point box: no ray with t < 1e30 enters it
+                hi[k] = 1e30f;
+            }
+        }
+    };
+    // root: an inner node whose children are the build root's children (or the root leaf)
+    std::vector<const BuildNode *> kchild;   // per kernel node: two children
+    std::vector<int> stack_build;
+    {
+        const BuildNode &r = B.nodes[root];
+        const BuildNode *c0 = r.count ? &r : &B.nodes[r.left];
+        const BuildNode *c1 = r.count ? nullptr : &B.nodes[r.right];
+        kchild.push_back(c0);
+        kchild.push_back(c1);
+        knodes.resize(4);
+    }
+    for (size_t kn = 0; kn < kchild.size() / 2; ++kn) {
+        const BuildNode *c[2] = {kchild[2 * kn], kchild[2 * kn + 1]};
+        float lo[2][3], hi[2][3];
+        int link[2];
+        for (int s = 0; s < 2; ++s) {
+            box_of(c[s], lo[s], hi[s]);
+            if (!c[s]) {
+                link[s] = ~0;   // empty leaf, never entered
+            } else if (c[s]->count) {
+                link[s] = emit_leaf_link(*c[s]);
+            } else {
+                link[s] = (int)(kchild.size() / 2);
+                kchild.push_back(&B.nodes[c[s]->left]);
+                kchild.push_back(&B.nodes[c[s]->right]);
+                knodes.resize(knodes.size() + 4);
+            }
+        }
+        float4 *o = &knodes[4 * kn];
+        o[0] = make_float4(lo[0][0], hi[0][0], lo[0][1], hi[0][1]);
+        o[1] = make_float4(lo[1][0], hi[1][0], lo[1][1], hi[1][1]);
+        o[2] = make_float4(lo[0][2], hi[0][2], lo[1][2], hi[1][2]);
+        float l0, l1;
+        memcpy(&l0, &link[0], 4);
+        memcpy(&l1, &link[1], 4);
+        o[3] = make_float4(l0, l1, 0.0f, 0.0f);
+    }
+    const int n_knodes = (int)(knodes.size() / 4);
+    const int n_order = (int)order.size();
+
+    // triangle records
+    std::vector<float4> tri4(3 * (size_t)std::max(n_order, 1));
+    for (int i = 0; i < n_order; ++i) {
+        int t = order[i];
+        const float *p0 = d->verts + 3 * d->tris[3 * t], *p1 = d->verts + 3 * d->tris[3 * t + 1],
+                    *p2 = d->verts + 3 * d->tris[3 * t + 2];
+        float idf;
+        memcpy(&idf, &t, 4);
+        tri4[3 * i] = make_float4(p0[0], p0[1], p0[2], idf);
+        tri4[3 * i + 1] = make_float4(p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2], 0.0f);
+        tri4[3 * i + 2] = make_float4(p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2], 0.0f);
+    }
+    std::vector<double> ref64((size_t)nt * REF_N, 0.0);
+    std::vector<float2> refdf((size_t)nt * REF_N);
+    std::vector<uint4> attr(nt);
+    std::vector<float4> tng(nt);
+    for (int t = 0; t < nt; ++t) {
+        const float *p0 = d->verts + 3 * d->tris[3 * t], *p1 = d->verts + 3 * d->tris[3 * t + 1],
+                    *p2 = d->verts + 3 * d->tris[3 * t + 2];
+        double e1[3], e2[3], v0[3];
+        for (int c = 0; c < 3; ++c) { v0[c] = p0[c]; e1[c] = (double)p1[c] - p0[c]; e2[c] = (double)p2[c] - p0[c]; }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        double *r = &ref64[(size_t)t * REF_N];
+        if (nn > 0.0) {
+            r[0] = n[0]; r[1] = n[1]; r[2] = n[2];
+            r[3] = n[0] * v0[0] + n[1] * v0[1] + n[2] * v0[2];
+            // m1 = (e2 x n) / |n|^2, m2 = (n x e1) / |n|^2
+            r[4] = (e2[1] * n[2] - e2[2] * n[1]) / nn;
+            r[5] = (e2[2] * n[0] - e2[0] * n[2]) / nn;
+            r[6] = (e2[0] * n[1] - e2[1] * n[0]) / nn;
+            r[7] = (n[1] * e1[2] - n[2] * e1[1]) / nn;
+            r[8] = (n[2] * e1[0] - n[0] * e1[2]) / nn;
+            r[9] = (n[0] * e1[1] - n[1] * e1[0]) / nn;
+            double ln = sqrt(nn);
+            tng[t] = make_float4((float)(n[0] / ln), (float)(n[1] / ln), (float)(n[2] / ln), 0.0f);
+        } else {
+            tng[t] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+            r[2] = 1.0;
+        }
+        for (int k = 0; k < REF_N; ++k) {
+            float h = (float)r[k];
+            refdf[(size_t)t * REF_N + k] = make_float2(h, (float)(r[k] - (double)h));
+        }
+        attr[t] = make_uint4(d->tris[3 * t], d->tris[3 * t + 1], d->tris[3 * t + 2], d->tri_mat[t]);
+    }
+    std::vector<MatDev> mats(d->nm);
+    for (int m = 0; m < d->nm; ++m) {
+        const hpt_material &M = d->materials[m];
+        MatDev &o = mats[m];
+        o.kind = M.kind;
+        o.tex = M.tex;
+        o.emit_tex = M.emit_tex;
+        o.light = M.light;
+        for (int c = 0; c < 3; ++c) { o.albedo[c] = M.albedo[c]; o.Le[c] = M.Le[c]; }
+        o.rough = M.roughness;
+        o.ior = M.ior;
+    }
+    std::vector<LightDev> lights(std::max(d->nl, 1));
+    for (int l = 0; l < d->nl; ++l) {
+        const float *L = d->lights + 12 * l;
+        LightDev &o = lights[l];
+        for (int c = 0; c < 3; ++c) { o.corner[c] = L[c]; o.eu[c] = L[3 + c]; o.ev[c] = L[6 + c]; o.Le[c] = L[9 + c]; }
+        double eu[3] = {L[3], L[4], L[5]}, ev[3] = {L[6], L[7], L[8]};
+        double n[3] = {eu[1] * ev[2] - eu[2] * ev[1], eu[2] * ev[0] - eu[0] * ev[2], eu[0] * ev[1] - eu[1] * ev[0]};
+        double a = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(a > 0.0)) return fail(HPT_ERR_INVALID_ARG, "light %d has zero area", l);
+        for (int c = 0; c < 3; ++c) o.n[c] = (float)(n[c] / a);
+        o.area = (float)a;
+    }
+    // one arena for everything
+    struct Part { const void *src; size_t bytes; size_t off; };
+    std::vector<Part> parts;
+    size_t off = 0;
+    auto add = [&](const void *src, size_t bytes) {
+        size_t o = off;
+        parts.push_back({src, bytes, o});
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    size_t o_nodes = add(knodes.data(), knodes.size() * sizeof(float4));
+    size_t o_tri4 = add(tri4.data(), tri4.size() * sizeof(float4));
+    size_t o_r64 = add(ref64.data(), ref64.size() * sizeof(double));
+    size_t o_rdf = add(refdf.data(), refdf.size() * sizeof(float2));
+    size_t o_attr = add(attr.data(), attr.size() * sizeof(uint4));
+    size_t o_ng = add(tng.data(), tng.size() * sizeof(float4));
+    size_t o_v = add(d->verts, (size_t)nv * 3 * sizeof(float));
+    size_t o_n = add(d->normals, (size_t)nv * 3 * sizeof(float));
+    size_t o_uv = add(d->uvs, (size_t)nv * 2 * sizeof(float));
+    size_t o_m = add(mats.data(), mats.size() * sizeof(MatDev));
+    float zero3[3] = {0, 0, 0};
+    int zero_i[3] = {0, 0, 0};
+    size_t o_tex = d->ntex > 0 ? add(d->tex_data, (size_t)d->tex_floats * sizeof(float)) : add(zero3, sizeof zero3);
+    size_t o_ti = d->ntex > 0 ? add(d->tex_info, (size_t)d->ntex * 3 * sizeof(int)) : add(zero_i, sizeof zero_i);
+    size_t o_l = add(lights.data(), lights.size() * sizeof(LightDev));
+    double zero4[4] = {0, 0, 0, 0};
+    size_t o_p = d->np > 0 ? add(d->points, (size_t)d->np * 4 * sizeof(double)) : add(zero4, sizeof zero4);
+    size_t cache_elems = (size_t)d->cache_res * d->cache_res * d->cache_res * 3;
+    uint16_t zero_h[4] = {0, 0, 0, 0};
+    size_t o_c = d->cache_res > 0 ? add(d->cache_E, cache_elems * sizeof(uint16_t)) : add(zero_h, sizeof zero_h);
+
+    auto rec = std::make_unique<SceneRec>();
+    CUDA_TRY(cudaMalloc(&rec->arena, off));
+    rec->bytes = off;
+    char *base = (char *)rec->arena;
+    for (auto &p : parts) {
+        cudaError_t e = cudaMemcpy(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(rec->arena);
+            return fail(HPT_ERR_CUDA, "scene copy: %s", cudaGetErrorString(e));
+        }
+    }
+    DevScene &s = rec->dev;
+    s.nodes = (const float4 *)(base + o_nodes);
+    s.tri4 = (const float4 *)(base + o_tri4);
+    s.ref64 = (const double *)(base + o_r64);
+    s.refdf = (const float2 *)(base + o_rdf);
+    s.tri_attr = (const uint4 *)(base + o_attr);
+    s.tri_ng = (const float4 *)(base + o_ng);
+    s.verts = (const float *)(base + o_v);
+    s.normals = (const float *)(base + o_n);
+    s.uvs = (const float *)(base + o_uv);
+    s.mats = (const MatDev *)(base + o_m);
+    s.tex = (const float *)(base + o_tex);
+    s.tex_info = (const int *)(base + o_ti);
+    s.lights = (const LightDev *)(base + o_l);
+    s.points = (const double *)(base + o_p);
+    s.cache = (const unsigned short *)(base + o_c);
+    for (int c = 0; c < 3; ++c) { s.cache_bmin[c] = d->cache_bmin[c]; s.cache_bmax[c] = d->cache_bmax[c]; }
+    s.cache_res = d->cache_res;
+    s.n_tris = nt;
+    s.n_nodes = n_knodes;
+    s.n_lights = d->nl;
+    s.n_points = d->np;
+    rec->n_nodes = n_knodes;
+    rec->depth = B.max_depth_seen;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    uint64_t id = ctx->next_scene++;
+    ctx->scenes[id] = std::move(rec);
+    *scene_id = id;
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_scene_release(hpt_ctx *ctx, uint64_t scene_id)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    std::unique_ptr<SceneRec> rec;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->scenes.find(scene_id);
+        if (it == ctx->scenes.end()) return fail(HPT_ERR_NOT_FOUND, "unknown scene %llu", (unsigned long long)scene_id);
+        if (it->second->users.load() > 0) return fail(HPT_ERR_BUSY, "scene %llu is used by queued requests", (unsigned long long)scene_id);
+        rec = std::move(it->second);
+        ctx->scenes.erase(it);
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaFree(rec->arena));
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_scene_info(hpt_ctx *ctx, uint64_t scene_id, uint64_t *bytes, int32_t *n_nodes, int32_t *depth)
+{
+    g_err.clear();
+    if (!ctx) return fail(HPT_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return fail(HPT_ERR_NOT_FOUND, "unknown scene %llu", (unsigned long long)scene_id);
+    if (bytes) *bytes = it->second->bytes;
+    if (n_nodes) *n_nodes = it->second->n_nodes;
+    if (depth) *depth = it->second->depth;
+    return HPT_OK;
+}
+
+// ---------------------------------------------------------------------- render -> job
+static hpt_status make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *r, void *out, size_t out_bytes,
+                           DevJob &J, SceneRec **rec_out)
+{
+    if (!r) return fail(HPT_ERR_INVALID_ARG, "render desc is NULL");
+    if (r->W <= 0 || r->H <= 0 || (int64_t)r->W * r->H > (1ll << 31))
+        return fail(HPT_ERR_INVALID_ARG, "bad SLM size %dx%d", r->W, r->H);
+    if (!(r->pitch > 0.0) || !std::isfinite(r->pitch)) return fail(HPT_ERR_INVALID_ARG, "bad pitch");
+    if (r->n_lambda < 1 || r->n_lambda > 3) return fail(HPT_ERR_INVALID_ARG, "n_lambda must be 1..3");
+    if (r->spp < 1 || r->max_depth < 1 || r->max_depth > 64) return fail(HPT_ERR_INVALID_ARG, "bad spp or max_depth");
+    if (r->K < 1 || r->K > KMAX) return fail(HPT_ERR_INVALID_ARG, "K must be 1..%d", KMAX);
+    if (r->hologram_offset < 0 || r->hologram_offset + r->K > (1 << 18)) return fail(HPT_ERR_INVALID_ARG, "bad hologram_offset");
+    if (r->phase_mode != HPT_PHASE_HASH && r->phase_mode != HPT_PHASE_ZERO) return fail(HPT_ERR_INVALID_ARG, "bad phase_mode");
+    if (r->precision != HPT_PREC_FP64 && r->precision != HPT_PREC_DF32) return fail(HPT_ERR_INVALID_ARG, "bad precision");
+    if (!(r->facet_size > 0.0) || !std::isfinite(r->facet_size)) return fail(HPT_ERR_INVALID_ARG, "bad facet_size");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(r->T[i])) return fail(HPT_ERR_INVALID_ARG, "non-finite T");
+    // rigid: orthonormal rotation block, last row (0, 0, 0, 1)
+    const double *T = r->T;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double dp = T[4 * a] * T[4 * b] + T[4 * a + 1] * T[4 * b + 1] + T[4 * a + 2] * T[4 * b + 2];
+            if (std::fabs(dp - (a == b ? 1.0 : 0.0)) > 1e-9) return fail(HPT_ERR_INVALID_ARG, "T is not rigid");
+        }
+    if (T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0) return fail(HPT_ERR_INVALID_ARG, "T last row must be 0 0 0 1");
+    const double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) + T[2] * (T[4] * T[9] - T[5] * T[8]);
+    if (det < 0.0) return fail(HPT_ERR_INVALID_ARG, "T must be a proper rotation");
+    size_t need = (size_t)8 * r->n_lambda * r->K * (size_t)r->W * r->H;
+    if (out && out_bytes < need) return fail(HPT_ERR_INVALID_ARG, "out_bytes %zu < %zu", out_bytes, need);
+    SceneRec *rec;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->scenes.find(scene_id);
+        if (it == ctx->scenes.end()) return fail(HPT_ERR_NOT_FOUND, "unknown scene %llu", (unsigned long long)scene_id);
+        rec = it->second.get();
+    }
+    if (r->use_cache && rec->dev.cache_res <= 0) return fail(HPT_ERR_INVALID_ARG, "use_cache set but the scene has no cache");
+    memset(&J, 0, sizeof J);
+    J.sc = rec->dev;
+    J.out = (float2 *)out;
+    J.W = r->W;
+    J.H = r->H;
+    J.n_lambda = r->n_lambda;
+    J.spp = r->spp;
+    J.max_depth = r->max_depth;
+    J.K = r->K;
+    J.hologram_offset = r->hologram_offset;
+    J.phase_mode = r->phase_mode;
+    J.use_cache = r->use_cache ? 1 : 0;
+    J.n_tiles_x = (r->W + TILE_W - 1) / TILE_W;
+    J.n_tiles = J.n_tiles_x * ((r->H + TILE_H - 1) / TILE_H);
+    J.n_items = (long long)r->n_lambda * J.n_tiles * 32;
+    J.seed_lo = (unsigned)r->seed;
+    J.seed_hi = (unsigned)(r->seed >> 32);
+    J.pseed_lo = (unsigned)r->phase_seed;
+    J.pseed_hi = (unsigned)(r->phase_seed >> 32);
+    for (int c = 0; c < r->n_lambda; ++c) {
+        double lam = r->lambda[c];
+        if (!(lam > 0.0) || !(lam < 2.0 * r->pitch)) return fail(HPT_ERR_INVALID_ARG, "lambda[%d] must be in (0, 2 pitch)", c);
+        if (r->channel[c] < 0 || r->channel[c] > 2) return fail(HPT_ERR_INVALID_ARG, "channel[%d] must be 0..2", c);
+        double thmax = asin(lam / (2.0 * r->pitch));
+        double sh = sin(0.5 * thmax);
+        double h = 2.0 * sh * sh;
+        J.channel[c] = r->channel[c];
+        J.lambda_f[c] = (float)lam;
+        J.pdf_w[c] = (float)(1.0 / (2.0 * M_PI * h));
+        J.cos_max[c] = (float)cos(thmax);
+        J.lambda[c] = make_rc(lam);
+        J.inv_lambda[c] = make_rc(1.0 / lam);
+        J.h_cone[c] = make_rc(h);
+    }
+    J.pitch = make_rc(r->pitch);
+    J.inv_facet = make_rc(1.0 / r->facet_size);
+    bool ident = true;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            J.R[3 * a + b] = make_rc(T[4 * a + b]);
+            if (T[4 * a + b] != (a == b ? 1.0 : 0.0)) ident = false;
+        }
+        J.t[a] = make_rc(T[4 * a + 3]);
+        if (T[4 * a + 3] != 0.0) ident = false;
+    }
+    J.t_identity = ident ? 1 : 0;
+    J.sincos_tab = ctx->d_sincos;
+    if (rec_out) *rec_out = rec;
+    return HPT_OK;
+}
+
+// ---------------------------------------------------------------------------- launches
+static Slot *acquire_slot(hpt_ctx *ctx)
+{
+    Slot *s = &ctx->slots[ctx->next_slot];
+    ctx->next_slot = (ctx->next_slot + 1) % hpt_ctx::NSLOTS;
+    if (s->used) cudaEventSynchronize(s->done);
+    s->used = true;
+    return s;
+}
+
+// queue one persistent launch over 'jobs' on stream s
+static hpt_status launch_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t s,
+                              Slot **slot_out)
+{
+    Slot *slot = acquire_slot(ctx);
+    JobTable *h = slot->h_table;
+    h->n_jobs = n;
+    long long items = 0;
+    for (int i = 0; i < n; ++i) {
+        h->jobs[i] = jobs[i];
+        h->jobs[i].item_start = items;
+        items += jobs[i].n_items;
+    }
+    h->total_items = items;
+    size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
+    CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(&slot->d_scratch->next_item, 0, sizeof(unsigned long long), s));
+    if (stats) CUDA_TRY(cudaMemsetAsync(slot->d_scratch->counters, 0, sizeof(slot->d_scratch->counters), s));
+    long long max_grid = (items + BLOCK - 1) / BLOCK;
+    int grid = (int)std::min<long long>((long long)ctx->sm_count * ctx->bps[prec], std::max<long long>(max_grid, 1));
+    CUDA_TRY(launch_trace(prec, stats, slot->d_table, slot->d_scratch, grid, s));
+    CUDA_TRY(cudaEventRecord(slot->done, s));
+    if (slot_out) *slot_out = slot;
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_dev,
+                                size_t out_bytes, void *stream)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_dev) return fail(HPT_ERR_INVALID_ARG, "out_dev is NULL");
+    DevJob J;
+    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return launch_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_host,
+                                     size_t out_bytes, void *stream)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_host || !desc) return fail(HPT_ERR_INVALID_ARG, "out_host or desc is NULL");
+    DevJob J;
+    st = make_job(ctx, scene_id, desc, nullptr, 0, J, nullptr);
+    if (st) return st;
+    size_t need = (size_t)8 * desc->n_lambda * desc->K * (size_t)desc->W * desc->H;
+    if (out_bytes < need) return fail(HPT_ERR_INVALID_ARG, "out_bytes %zu < %zu", out_bytes, need);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->host_out_bytes < need) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
+        ctx->host_out_dev = nullptr;
+        ctx->host_out_bytes = 0;
+        CUDA_TRY(cudaMalloc(&ctx->host_out_dev, need));
+        ctx->host_out_bytes = need;
+    }
+    J.out = (float2 *)ctx->host_out_dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = launch_jobs(ctx, &J, 1, desc->precision, false, s, nullptr);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out_dev, need, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return HPT_OK;
+}
+
+static hpt_status read_status(hpt_ctx *ctx)
+{
+    unsigned bits = 0;
+    for (auto &s : ctx->slots) {
+        unsigned v = 0;
+        CUDA_TRY(cudaMemcpy(&v, &s.d_scratch->status, sizeof v, cudaMemcpyDeviceToHost));
+        if (v) {
+            bits |= v;
+            CUDA_TRY(cudaMemset(&s.d_scratch->status, 0, sizeof v));
+        }
+    }
+    if (bits)
+        return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
+                    (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_sync(hpt_ctx *ctx)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return read_status(ctx);
+}
+
+extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_dev,
+                                         size_t out_bytes, uint64_t counters[HPT_NCOUNTERS])
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_dev || !counters) return fail(HPT_ERR_INVALID_ARG, "out_dev or counters is NULL");
+    DevJob J;
+    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Slot *slot = nullptr;
+    st = launch_jobs(ctx, &J, 1, desc->precision, true, 0, &slot);
+    if (st) return st;
+    CUDA_TRY(cudaStreamSynchronize(0));
+    unsigned long long c[8];
+    CUDA_TRY(cudaMemcpy(c, slot->d_scratch->counters, sizeof c, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k];
+    return read_status(ctx);
+}
+
+// ------------------------------------------------------------------------------ serving
+static void sched_loop(hpt_ctx *ctx) { (void)ctx; }
+
+extern "C" hpt_status hpt_submit(hpt_ctx *, uint64_t, const hpt_render_desc *, void *, size_t, uint64_t *)
+{
+    return fail(HPT_ERR_UNSUPPORTED, "serving not built yet");
+}
+extern "C" hpt_status hpt_poll(hpt_ctx *, uint64_t, int *) { return fail(HPT_ERR_UNSUPPORTED, "serving not built yet"); }
+extern "C" hpt_status hpt_wait(hpt_ctx *, uint64_t, uint32_t) { return fail(HPT_ERR_UNSUPPORTED, "serving not built yet"); }
+extern "C" hpt_status hpt_request_times(hpt_ctx *, uint64_t, double *)
+{
+    return fail(HPT_ERR_UNSUPPORTED, "serving not built yet");
+}

@@ -1,0 +1,101 @@
+// Internal layouts shared by the host runtime and the device kernels of the wave path tracer.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hpt {
+
+constexpr int KMAX = 8;            // holograms per path set held by one thread
+constexpr int BLOCK = 128;         // threads per block of the trace kernel
+constexpr int STACK = 64;          // traversal stack entries per thread (shared memory)
+constexpr int MAX_JOBS = 64;       // jobs (requests) in one persistent launch
+constexpr int TILE_W = 8, TILE_H = 4;
+
+// status bits written by the kernels
+enum : uint32_t { ST_STACK_OVERFLOW = 1u, ST_BAD_JOB = 2u, ST_FALLBACK_STACK = 4u };
+
+// A constant needed by the coherent chain in both arithmetics: the double value and
+// its double-float split (hi = rn(x), lo = rn(x - hi)).
+struct RC {
+    double d;
+    float hi, lo;
+};
+
+struct alignas(16) MatDev {
+    int kind, tex, emit_tex, light;
+    float albedo[3];
+    float rough;
+    float ior;
+    float Le[3];
+};
+
+struct alignas(16) LightDev {
+    float corner[3], eu[3], ev[3], Le[3];
+    float n[3];       // unit normal (eu x ev)
+    float area;
+};
+
+// Per-triangle record for the high-precision refinement (indexed by the input triangle id):
+// plane n . x = d0 with n = e1 x e2 (unnormalised), and the rows m1, m2 that give the
+// barycentrics b1 = m1 . (x - v0), b2 = m2 . (x - v0) of a point on the plane.
+constexpr int REF_N = 10;   // n.xyz, d0, m1.xyz, m2.xyz
+
+struct DevScene {
+    const float4 *nodes;      // 4 float4 per BVH2 node (child boxes + child links)
+    const float4 *tri4;       // 3 float4 per triangle in leaf order: (v0, id), e1, e2
+    const double *ref64;      // [nt][REF_N]
+    const float2 *refdf;      // [nt][REF_N] (hi, lo)
+    const uint4 *tri_attr;    // [nt] vertex indices i0, i1, i2, material
+    const float4 *tri_ng;     // [nt] unit geometric normal (winding)
+    const float *verts;       // [nv][3]
+    const float *normals;     // [nv][3]
+    const float *uvs;         // [nv][2]
+    const MatDev *mats;
+    const float *tex;
+    const int *tex_info;      // [ntex][3]
+    const LightDev *lights;
+    const double *points;     // [np][4]
+    const unsigned short *cache;   // binary16 [res][res][res][3]
+    float cache_bmin[3], cache_bmax[3];
+    int cache_res;
+    int n_tris, n_nodes, n_lights, n_points;
+};
+
+struct DevJob {
+    DevScene sc;
+    float2 *out;                // [n_lambda][K][H][W]
+    long long item_start;       // first global work item of this job
+    long long n_items;          // n_lambda * n_tiles * 32
+    int W, H, n_lambda, spp, max_depth, K, hologram_offset, phase_mode, use_cache;
+    int t_identity;
+    int n_tiles_x, n_tiles;
+    int channel[3];
+    unsigned seed_lo, seed_hi, pseed_lo, pseed_hi;
+    float lambda_f[3];
+    float pdf_w[3];             // 1 / (2 pi (1 - cos theta_max))
+    float cos_max[3];           // cos theta_max (float) for the point-emitter cone mask
+    RC lambda[3];
+    RC inv_lambda[3];
+    RC h_cone[3];               // 1 - cos theta_max = 2 sin^2(theta_max / 2)
+    RC pitch;
+    RC inv_facet;
+    RC R[9];                    // rotation of T (world -> hologram), row-major
+    RC t[3];                    // translation of T
+    const float4 *sincos_tab;   // cos/sin(2 pi k / 256) as (hi, lo) float pairs, 256 entries
+};
+
+struct JobTable {
+    int n_jobs;
+    long long total_items;
+    DevJob jobs[MAX_JOBS];
+};
+
+// device-side scratch of one launch slot
+struct SlotScratch {
+    unsigned long long next_item;   // work counter (reset before every launch)
+    unsigned int status;            // error bits (sticky until read by hpt_sync)
+    unsigned int pad;
+    unsigned long long counters[8];
+};
+
+}  // namespace hpt

@@ -1,0 +1,269 @@
+"""Python binding of the C-ABI in include/hpt.h (argument marshalling only).
+
+Every step of the wave path tracer runs in the CUDA library ``_lib/libhpt.so``;
+this module only packs numpy arrays and torch device buffers into the C structs.
+It raises if the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhpt.so")
+
+HPT_OK = 0
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY",
+                -6: "NOT_FOUND", -7: "UNSUPPORTED", -8: "DEVICE"}
+PREC_FP64, PREC_DF32 = 0, 1
+NCOUNTERS = 8
+COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_fallbacks", "shadow_rays", "bounces"]
+
+# exported symbols, as declared in include/hpt.h
+SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
+           "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
+           "hpt_request_times"]
+
+
+class HptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CtxDesc(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_inflight", C.c_int32), ("flags", C.c_int32)]
+
+
+class Material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("albedo", C.c_float * 3), ("roughness", C.c_float), ("ior", C.c_float),
+                ("Le", C.c_float * 3), ("tex", C.c_int32), ("emit_tex", C.c_int32), ("light", C.c_int32)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("nv", C.c_int32), ("nt", C.c_int32), ("nm", C.c_int32), ("ntex", C.c_int32), ("nl", C.c_int32),
+                ("np", C.c_int32), ("verts", C.c_void_p), ("normals", C.c_void_p), ("uvs", C.c_void_p),
+                ("tris", C.c_void_p), ("tri_mat", C.c_void_p), ("materials", C.c_void_p), ("tex_data", C.c_void_p),
+                ("tex_floats", C.c_int64), ("tex_info", C.c_void_p), ("lights", C.c_void_p), ("points", C.c_void_p),
+                ("cache_res", C.c_int32), ("cache_bmin", C.c_float * 3), ("cache_bmax", C.c_float * 3),
+                ("cache_E", C.c_void_p)]
+
+
+class RenderDesc(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("pitch", C.c_double), ("n_lambda", C.c_int32),
+                ("lam", C.c_double * 3), ("channel", C.c_int32 * 3), ("spp", C.c_int32), ("max_depth", C.c_int32),
+                ("K", C.c_int32), ("hologram_offset", C.c_int32), ("seed", C.c_uint64), ("phase_seed", C.c_uint64),
+                ("phase_mode", C.c_int32), ("facet_size", C.c_double), ("T", C.c_double * 16),
+                ("precision", C.c_int32), ("use_cache", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhpt.so (no fallback: a missing library is an error)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    vp, st = C.c_void_p, C.c_int
+    lib.hpt_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(CtxDesc)]
+    lib.hpt_destroy.argtypes = [vp]
+    lib.hpt_destroy.restype = None
+    lib.hpt_last_error.restype = C.c_char_p
+    lib.hpt_scene_upload.argtypes = [vp, C.POINTER(SceneDesc), C.POINTER(C.c_uint64)]
+    lib.hpt_scene_release.argtypes = [vp, C.c_uint64]
+    lib.hpt_scene_info.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.hpt_trace.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
+    lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
+    lib.hpt_sync.argtypes = [vp]
+    lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_submit.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
+    lib.hpt_wait.argtypes = [vp, C.c_uint64, C.c_uint32]
+    lib.hpt_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double)]
+    for name in SYMBOLS:
+        f = getattr(lib, name)
+        if name not in ("hpt_destroy", "hpt_last_error"):
+            f.restype = st
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != HPT_OK:
+        raise HptError(status, load_library().hpt_last_error().decode())
+
+
+def render_desc(r, precision=PREC_DF32) -> RenderDesc:
+    d = RenderDesc()
+    d.W, d.H, d.pitch = int(r.W), int(r.H), float(r.pitch)
+    d.n_lambda = len(r.lambdas)
+    for i, (l, c) in enumerate(zip(r.lambdas, r.channels)):
+        d.lam[i] = float(l)
+        d.channel[i] = int(c)
+    d.spp, d.max_depth, d.K, d.hologram_offset = int(r.spp), int(r.max_depth), int(r.K), int(r.hologram_offset)
+    d.seed, d.phase_seed, d.phase_mode = int(r.seed), int(r.phase_seed), int(r.phase_mode)
+    d.facet_size = float(r.facet_size)
+    T = np.asarray(r.T, np.float64).reshape(16)
+    for i in range(16):
+        d.T[i] = float(T[i])
+    d.precision = int(precision)
+    d.use_cache = int(r.use_cache)
+    return d
+
+
+def out_bytes(r) -> int:
+    return 8 * len(r.lambdas) * int(r.K) * int(r.W) * int(r.H)
+
+
+class Context:
+    """One library context on one CUDA device (owns scenes and launch slots)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0):
+        self.lib = load_library()
+        self.h = C.c_void_p()
+        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0)
+        _check(self.lib.hpt_create(C.byref(self.h), int(device), C.byref(desc)))
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.hpt_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- scenes
+    def upload_scene(self, s) -> int:
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        nm = len(s.mat_type)
+        mats = (Material * nm)()
+        for i in range(nm):
+            m = mats[i]
+            m.kind = int(s.mat_type[i])
+            for c in range(3):
+                m.albedo[c] = float(s.mat_albedo[i, c])
+                m.Le[c] = float(s.mat_Le[i, c])
+            m.roughness = float(s.mat_rough[i])
+            m.ior = float(s.mat_ior[i])
+            m.tex = int(s.mat_tex[i])
+            m.emit_tex = int(s.mat_emit_tex[i])
+            m.light = int(s.mat_light[i])
+        d = SceneDesc()
+        d.nv, d.nt, d.nm = len(s.verts), len(s.tris), nm
+        d.ntex, d.nl, d.np = len(s.tex_info), len(s.lights), len(s.points)
+        d.verts = arr(s.verts, np.float32)
+        d.normals = arr(s.normals, np.float32)
+        d.uvs = arr(s.uvs, np.float32)
+        d.tris = arr(s.tris, np.uint32)
+        d.tri_mat = arr(s.tri_mat, np.uint32)
+        d.materials = C.cast(mats, C.c_void_p)
+        d.tex_data = arr(s.tex_data, np.float32)
+        d.tex_floats = int(np.asarray(s.tex_data).size)
+        d.tex_info = arr(s.tex_info, np.int32)
+        d.lights = arr(s.lights, np.float32) if len(s.lights) else None
+        d.points = arr(s.points, np.float64) if len(s.points) else None
+        d.cache_res = int(s.cache_res)
+        if s.cache_res:
+            for c in range(3):
+                d.cache_bmin[c] = float(s.cache_bmin[c])
+                d.cache_bmax[c] = float(s.cache_bmax[c])
+            d.cache_E = arr(np.asarray(s.cache_E).view(np.uint16), np.uint16)
+        sid = C.c_uint64()
+        _check(self.lib.hpt_scene_upload(self.h, C.byref(d), C.byref(sid)))
+        return sid.value
+
+    def release_scene(self, sid: int):
+        _check(self.lib.hpt_scene_release(self.h, C.c_uint64(sid)))
+
+    def scene_info(self, sid: int):
+        b, n, dep = C.c_uint64(), C.c_int32(), C.c_int32()
+        _check(self.lib.hpt_scene_info(self.h, C.c_uint64(sid), C.byref(b), C.byref(n), C.byref(dep)))
+        return {"device_bytes": b.value, "nodes": n.value, "depth": dep.value}
+
+    # ----------------------------------------------------------------- traces
+    def trace(self, sid: int, r, out, precision=PREC_DF32, stream=None):
+        """Asynchronous trace into a caller-owned device buffer (a torch complex64 CUDA tensor
+        of shape (n_lambda, K, H, W), or a raw device pointer with out_nbytes given by out_bytes(r))."""
+        ptr, nbytes = _dev_buffer(out, r)
+        d = render_desc(r, precision)
+        _check(self.lib.hpt_trace(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, _stream_ptr(stream)))
+
+    def trace_host(self, sid: int, r, out_host: np.ndarray, precision=PREC_DF32, stream=None):
+        """End-to-end trace into host memory (numpy complex64 array, pinned or pageable)."""
+        assert out_host.dtype == np.complex64 and out_host.flags.c_contiguous
+        d = render_desc(r, precision)
+        _check(self.lib.hpt_trace_host(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(out_host.ctypes.data),
+                                       out_host.nbytes, _stream_ptr(stream)))
+
+    def trace_counters(self, sid: int, r, out, precision=PREC_DF32):
+        ptr, nbytes = _dev_buffer(out, r)
+        d = render_desc(r, precision)
+        c = (C.c_uint64 * NCOUNTERS)()
+        _check(self.lib.hpt_trace_counters(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, c))
+        return dict(zip(COUNTER_NAMES, [int(x) for x in c]))
+
+    def sync(self):
+        _check(self.lib.hpt_sync(self.h))
+
+    # ---------------------------------------------------------------- serving
+    def submit(self, sid: int, r, out, precision=PREC_DF32) -> int:
+        ptr, nbytes = _dev_buffer(out, r) if out is not None else (0, 0)
+        d = render_desc(r, precision)
+        rid = C.c_uint64()
+        _check(self.lib.hpt_submit(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = C.c_int()
+        _check(self.lib.hpt_poll(self.h, C.c_uint64(rid), C.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: int = 0):
+        _check(self.lib.hpt_wait(self.h, C.c_uint64(rid), int(timeout_ms)))
+
+    def request_times(self, rid: int):
+        t = (C.c_double * 3)()
+        _check(self.lib.hpt_request_times(self.h, C.c_uint64(rid), t))
+        return tuple(t)
+
+
+def _dev_buffer(out, r):
+    need = out_bytes(r)
+    if isinstance(out, int):
+        return out, need
+    import torch  # device memory only
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CUDA tensor or a device pointer")
+    nbytes = out.numel() * out.element_size()
+    if nbytes < need:
+        raise ValueError(f"output buffer has {nbytes} bytes, need {need}")
+    return out.data_ptr(), nbytes
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def alloc_output(r, device="cuda"):
+    import torch
+    return torch.empty((len(r.lambdas), int(r.K), int(r.H), int(r.W)), dtype=torch.complex64, device=device)

@@ -1,0 +1,189 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle, on a GB300.
+
+Each case renders the same seeded synthetic input on both sides and compares every pixel
+of every (wavelength, hologram) output: relative error <= 1e-4 and phase error <= 1e-3 rad
+on >= 99.9 % of pixels (tests/parity.py).  Both coherent arithmetics are checked: native
+FP64 and double-float (DF32).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_14173_gb300 import scenes as S
+from tests.parity import assert_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [0, 1]   # HPT_PREC_FP64, HPT_PREC_DF32
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2606_14173_gb300 import build, hpt
+    build.build()
+    c = hpt.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_trace(ctx, sid, r, prec):
+    from paper_2606_14173_gb300 import hpt
+    out = hpt.alloc_output(r)
+    ctx.trace(sid, r, out, precision=prec)
+    ctx.sync()
+    return out.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def cfg0(ctx, oracle_mod):
+    sc = S.config0_scene()
+    return sc, ctx.upload_scene(sc), oracle_mod.Oracle(sc)
+
+
+@pytest.fixture(scope="module")
+def cfg1(ctx, oracle_mod):
+    sc = S.config1_scene()
+    return sc, ctx.upload_scene(sc), oracle_mod.Oracle(sc)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config0_full_frame(ctx, cfg0, prec):
+    sc, sid, orc = cfg0
+    r = S.config0_render()
+    U = gpu_trace(ctx, sid, r, prec)
+    ref = orc.trace_full(r)
+    reps = assert_parity(U, ref, f"cfg0 prec={prec}")
+    assert reps[0]["rms"] > 1.0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_scene_ragged_crop(ctx, cfg1, prec):
+    """The icosphere scene with every material, depth 4, RGB, on an SLM of ragged size."""
+    sc, sid, orc = cfg1
+    r = S.config1_render(W=203, H=117, spp=8, K=2)
+    U = gpu_trace(ctx, sid, r, prec)
+    ref = orc.trace_full(r)
+    assert_parity(U, ref, f"cfg1 crop prec={prec}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_headline_config_full_size_sampled(ctx, cfg1, prec):
+    """1920x1080, RGB, 64 spp, depth 4, K = 8 -- the launch the benchmark times -- checked on a
+    64x64 tile plus 1024 random pixels computed by the oracle one by one."""
+    sc, sid, orc = cfg1
+    r = S.config2_render()
+    U = gpu_trace(ctx, sid, r, prec)
+    assert U.shape == (3, 8, 1080, 1920)
+    rng = np.random.default_rng(11)
+    tile = (np.arange(900, 964)[:, None] * r.W + np.arange(1000, 1064)[None, :]).reshape(-1)
+    pix = np.concatenate([tile, rng.choice(r.W * r.H, 1024, replace=False)])
+    ref = orc.trace(r, pix)
+    got = U.reshape(3, 8, -1)[:, :, pix]
+    assert_parity(got, ref, f"cfg2 sampled prec={prec}")
+
+
+def test_precisions_agree(ctx, cfg1):
+    sc, sid, _ = cfg1
+    r = S.config1_render(W=160, H=96, spp=8)
+    a = gpu_trace(ctx, sid, r, 0)
+    b = gpu_trace(ctx, sid, r, 1)
+    assert compare(a[1, 0], b[1, 0])["frac_fail"] <= 1e-3
+
+
+def test_path_reuse_index_invariance_bitwise(ctx, cfg0):
+    sc, sid, _ = cfg0
+    r8 = S.config0_render(W=96, H=72, spp=4, K=8)
+    U8 = gpu_trace(ctx, sid, r8, 1)
+    for m in (0, 5, 7):
+        U1 = gpu_trace(ctx, sid, S.config0_render(W=96, H=72, spp=4, K=1, hologram_offset=m), 1)
+        assert np.array_equal(U8[:, m], U1[:, 0])
+    Uz = gpu_trace(ctx, sid, S.config0_render(W=96, H=72, spp=4, K=3, phase_mode=S.PHASE_ZERO), 1)
+    assert np.array_equal(Uz[:, 1], Uz[:, 0]) and np.array_equal(Uz[:, 2], Uz[:, 0])
+
+
+def test_deterministic_bitwise(ctx, cfg1):
+    sc, sid, _ = cfg1
+    r = S.config1_render(W=64, H=40, spp=4)
+    assert np.array_equal(gpu_trace(ctx, sid, r, 1), gpu_trace(ctx, sid, r, 1))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_point_emitter_spherical_wave(ctx, prec):
+    """Phase and distance precision: a point emitter gives a e^{ikr} cos(theta)/r (closed form)."""
+    pts = [(1e-4, -2e-4, 5e-3, 1e-3), (-3e-4, 1e-4, 2.5e-2, 3e-3)]
+    sc = S.point_emitter_scene(pts)
+    sid = ctx.upload_scene(sc)
+    r = S.config0_render(W=128, H=96, spp=1)
+    U = gpu_trace(ctx, sid, r, prec)[0, 0]
+    lam = r.lambdas[0]
+    ii, jj = np.meshgrid(np.arange(r.W), np.arange(r.H))
+    x = (ii + 0.5 - r.W / 2) * r.pitch
+    y = (jj + 0.5 - r.H / 2) * r.pitch
+    cmax = math.sqrt(1 - (lam / (2 * r.pitch)) ** 2)
+    want = np.zeros(U.shape, np.complex128)
+    for (px, py, pz, a) in pts:
+        rr = np.sqrt((px - x) ** 2 + (py - y) ** 2 + pz ** 2)
+        c = pz / rr
+        want += np.where(c >= cmax, a * np.exp(2j * np.pi * rr / lam) * c / rr, 0)
+    rep = compare(U, want)
+    assert rep["frac_fail"] <= 1e-3 and rep["max_phase"] < 1e-4, rep
+    ctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mirror_and_transform_cases(ctx, oracle_mod, prec):
+    a, _ = S.mirror_pair_scenes()
+    r = S.config0_render(W=64, H=64, spp=8, max_depth=2)
+    sid = ctx.upload_scene(a)
+    assert_parity(gpu_trace(ctx, sid, r, prec), oracle_mod.Oracle(a).trace_full(r), "mirror")
+    ctx.release_scene(sid)
+    rot = S.rotate_z90(S.config0_scene())
+    r = S.config0_render(W=64, H=48, spp=6, T=S.ROT_Z_MINUS_90.copy())
+    sid = ctx.upload_scene(rot)
+    assert_parity(gpu_trace(ctx, sid, r, prec), oracle_mod.Oracle(rot).trace_full(r), "rotated")
+    ctx.release_scene(sid)
+
+
+def test_dielectric_slab_and_furnace(ctx, oracle_mod):
+    for sc, r in ((S.slab_scene(), S.config0_render(W=40, H=40, spp=16, max_depth=3)),
+                  (S.furnace_scene(), S.config0_render(W=32, H=32, spp=4, max_depth=3)),
+                  (S.lit_receiver_scene(S.GGX, albedo=0.8, rough=0.4), S.config0_render(W=48, H=32, spp=8, max_depth=2))):
+        sid = ctx.upload_scene(sc)
+        for prec in PRECS:
+            assert_parity(gpu_trace(ctx, sid, r, prec), oracle_mod.Oracle(sc).trace_full(r), sc.name)
+        ctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("W,H,spp,K", [(1, 1, 1, 1), (7, 3, 2, 8), (33, 5, 1, 3)])
+def test_tiny_and_ragged_sizes(ctx, cfg0, W, H, spp, K):
+    sc, sid, orc = cfg0
+    r = S.config0_render(W=W, H=H, spp=spp, K=K)
+    assert_parity(gpu_trace(ctx, sid, r, 1), orc.trace_full(r), f"{W}x{H}")
+
+
+def test_invalid_arguments_are_rejected(ctx, cfg0, torch_cuda):
+    from paper_2606_14173_gb300 import hpt
+    sc, sid, _ = cfg0
+    out = hpt.alloc_output(S.config0_render())
+    bad = [dict(K=9), dict(spp=0), dict(max_depth=0), dict(lambdas=(20e-6,)), dict(W=0),
+           dict(T=np.diag([1.0, 2.0, 1.0, 1.0])), dict(facet_size=0.0)]
+    for kw in bad:
+        with pytest.raises(hpt.HptError) as e:
+            ctx.trace(sid, S.config0_render(**kw), out)
+        assert e.value.status == -1, kw
+    with pytest.raises(hpt.HptError) as e:
+        ctx.trace(12345, S.config0_render(), out)
+    assert e.value.status == -6
+    small = torch_cuda.empty(10, dtype=torch_cuda.complex64, device="cuda")
+    with pytest.raises(ValueError):
+        ctx.trace(sid, S.config0_render(), small)
+    ctx.sync()
