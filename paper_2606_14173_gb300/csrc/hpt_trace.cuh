@@ -111,12 +111,14 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     h.u = h.v = 0.0f;
     if (TRACK) t_near = big;
     const float cull = TRACK ? (1.0f + 4.0f * TIE_REL) : 1.0f;
+    const float4 *__restrict__ nodes = sc.nodes;
+    const float4 *__restrict__ tris = sc.tri4;
     int sp = 0;
     int node = 0;
     for (;;) {
         // descend inner nodes
         while (node >= 0) {
-            const float4 *np = sc.nodes + 4 * node;
+            const float4 *np = nodes + 4 * node;
             float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
             float tl = h.t * cull;
             float a0 = n0.x * inv.x - ood.x, b0 = n0.y * inv.x - ood.x;
@@ -149,7 +151,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
         int code = ~node;
         int start = code >> 8, count = code & 255;
         for (int i = start; i < start + count; ++i) {
-            const float4 *tp = sc.tri4 + 3 * i;
+            const float4 *tp = tris + 3 * i;
             float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
             int id = __float_as_int(A.w);
             if (STATS) cnt.tris++;
@@ -435,7 +437,13 @@ template <class R> struct Lane {
     float3 ro, rd;
     float rtmax;
     int rskip;
+    // surface waiting for vertex processing
+    Surf surf;
+    float3 wo;
 };
+
+// what the main loop does next with a lane
+enum : int { A_COH = 0, A_SHADOW = 1, A_BOUNCE = 2, A_VERTEX = 3, A_FINISH = 4 };
 
 // s1 + s2: pixel centre, uniform direction in the cone theta <= asin(lambda / 2p), world space
 template <class R> __device__ __forceinline__ void start_sample(Lane<R> &st)
@@ -590,7 +598,7 @@ __device__ __forceinline__ int finish_sample(Lane<R> &st, float *acc, int *stk, 
 }
 
 // Sets the ray for the stored BSDF continuation.
-template <class R> __device__ __forceinline__ int take_bounce(Lane<R> &st)
+template <class R> __device__ __forceinline__ void take_bounce(Lane<R> &st)
 {
     st.ro = st.borg;
     st.rd = st.bdir;
@@ -599,15 +607,15 @@ template <class R> __device__ __forceinline__ int take_bounce(Lane<R> &st)
     st.beta = st.b_beta;
     st.prev_pdf = st.b_pdf;
     st.prev_delta = false;
-    return S_BOUNCE;
 }
 
 // s5: one vertex of the incoherent path: emission (MIS-weighted), then a delta continuation, or
 // the ambient cache, or NEE to a rectangular light plus a BSDF-sampled continuation.
-template <class R, bool STATS>
-__device__ __forceinline__ int vertex(Lane<R> &st, const Surf &S, float3 wo, float *acc, int *stk, int &status,
-                                     Counters &cnt)
+template <class R>
+__device__ __forceinline__ int vertex(Lane<R> &st)
 {
+    const Surf &S = st.surf;
+    const float3 wo = st.wo;
     const DevJob &J = *st.J;
     const DevScene &sc = J.sc;
     const MatDev M = sc.mats[S.mat];
@@ -623,34 +631,34 @@ __device__ __forceinline__ int vertex(Lane<R> &st, const Surf &S, float3 wo, flo
         }
         st.L += st.beta * Le * w;
     }
-    if (M.kind == 4) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+    if (M.kind == 4) return A_FINISH;
     float3 ng = S.ng, ns = S.ns;
     const bool front = dot3(wo, ng) > 0.0f;
     const float4 u = path_draw(J, st.pix, (unsigned)st.s, (unsigned)st.v, 0u, (unsigned)st.lam);
     if (M.kind == 2 || M.kind == 3) {
-        if (st.v >= J.max_depth) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        if (st.v >= J.max_depth) return A_FINISH;
         float3 wi;
         if (M.kind == 2) {
             if (!front) { ng = -ng; ns = -ns; }
             float c = dot3(wo, ns);
-            if (c <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            if (c <= 0.0f) return A_FINISH;
             wi = ns * (2.0f * c) - wo;
-            if (dot3(wi, ng) <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            if (dot3(wi, ng) <= 0.0f) return A_FINISH;
             st.beta *= albedo_of(sc, M, S, ch);
         } else {
             float n_i = front ? 1.0f : M.ior, n_t = front ? M.ior : 1.0f;
             float3 n = front ? ns : -ns, g = front ? ng : -ng;
             float ci = dot3(wo, n);
-            if (ci <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            if (ci <= 0.0f) return A_FINISH;
             float F = fresnel_dielectric(ci, n_i, n_t);
             if (u.x < F) {
                 wi = n * (2.0f * ci) - wo;
-                if (dot3(wi, g) <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+                if (dot3(wi, g) <= 0.0f) return A_FINISH;
             } else {
                 float eta = n_i / n_t;
                 float ct = sqrtf(fmaxf(0.0f, 1.0f - eta * eta * (1.0f - ci * ci)));
                 wi = wo * (-eta) + n * (eta * ci - ct);
-                if (dot3(wi, g) >= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+                if (dot3(wi, g) >= 0.0f) return A_FINISH;
                 st.beta *= eta * eta;
             }
         }
@@ -660,14 +668,14 @@ __device__ __forceinline__ int vertex(Lane<R> &st, const Surf &S, float3 wo, flo
         st.rd = wi;
         st.rtmax = 1e30f;
         st.rskip = S.tri;
-        return S_BOUNCE;
+        return A_BOUNCE;
     }
     // non-delta (Lambert, GGX)
     if (!front) { ng = -ng; ns = -ns; }
-    if (dot3(wo, ns) <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+    if (dot3(wo, ns) <= 0.0f) return A_FINISH;
     if (J.use_cache && sc.cache_res > 0 && !st.inc_first) {
         st.L += st.beta * albedo_of(sc, M, S, ch) * INV_PI_F * cache_lookup(sc, S.p, ch);
-        return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        return A_FINISH;
     }
     const float3 org = S.p + ng * INC_OFFSET;
     bool shadow = false;
@@ -756,18 +764,21 @@ __device__ __forceinline__ int vertex(Lane<R> &st, const Surf &S, float3 wo, flo
         st.rd = wl;
         st.rtmax = smax;
         st.rskip = S.tri;
-        return S_SHADOW;
+        return A_SHADOW;
     }
-    if (st.has_bounce) return take_bounce(st);
-    return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+    if (st.has_bounce) {
+        take_bounce(st);
+        return A_BOUNCE;
+    }
+    return A_FINISH;
 }
 
 // s3 + s4 for a coherent segment: decide the hit (float traversal, double re-decision when not
 // conclusive), refine the distance in the coherent arithmetic, then either the real image
 // point P (non-delta) or the next delta segment.
 template <class R, bool STATS>
-__device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float t_near, float *acc, int *stk,
-                                           int &status, Counters &cnt)
+__device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float t_near, int *stk, int &status,
+                                           Counters &cnt)
 {
     using RO = RealOps<R>;
     const DevJob &J = *st.J;
@@ -780,7 +791,7 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
                             RO::to_d(st.cd.y), RO::to_d(st.cd.z), st.cv > 0 ? COH_TMIN : 0.0, st.rskip, &tt, stk,
                             status);
     }
-    if (tri < 0) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+    if (tri < 0) return A_FINISH;
     if (STATS) cnt.refines++;
     // distance along the ray to the triangle's plane n . x = d0
     const int rb = tri * REF_N;
@@ -801,7 +812,8 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
                           RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 6)));
     const float3 m2f = f3(RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 7)), RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 8)),
                           RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 9)));
-    const Surf S = make_surf(sc, tri, tof3(P), dot3(m1f, dPf), dot3(m2f, dPf));
+    st.surf = make_surf(sc, tri, tof3(P), dot3(m1f, dPf), dot3(m2f, dPf));
+    const Surf &S = st.surf;
     if (kind != 2 && kind != 3) {
         // P: first non-delta hit = the real image point.  For a rigid T the virtual image point
         // Q = T (O + d_OPL v) lies at distance r = d_OPL from the pixel along the sampled
@@ -822,9 +834,10 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
         st.inc_first = true;
         st.prev_pdf = 0.0f;
         st.t_prev = 0.0f;
-        return vertex<R, STATS>(st, S, -dl, acc, stk, status, cnt);
+        st.wo = -dl;
+        return A_VERTEX;
     }
-    if (st.cv >= J.max_depth) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+    if (st.cv >= J.max_depth) return A_FINISH;
     // delta vertex: interpolated shading normal and the new direction in the coherent arithmetic
     const MatDev M = sc.mats[ix.w];
     R b1 = rdot(r3<R>(RO::load(sc.ref64, sc.refdf, rb + 4), RO::load(sc.ref64, sc.refdf, rb + 5),
@@ -843,9 +856,9 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
     if (kind == 2) {
         if (!front) { ns = neg(ns); ng = -ng; }
         R c = rdot(wo, ns);
-        if (!(RO::to_f(c) > 0.0f)) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        if (!(RO::to_f(c) > 0.0f)) return A_FINISH;
         wi = scale(ns, RO::mulf(c, 2.0f)) - wo;
-        if (dot3(tof3(wi), ng) <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        if (dot3(tof3(wi), ng) <= 0.0f) return A_FINISH;
         st.beta_c *= albedo_of(sc, M, S, st.ch);
     } else {
         const float n_i = front ? 1.0f : M.ior, n_t = front ? M.ior : 1.0f;
@@ -853,17 +866,17 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
         const float3 g = front ? ng : -ng;
         R ci = rdot(wo, nn);
         const float cif = RO::to_f(ci);
-        if (!(cif > 0.0f)) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        if (!(cif > 0.0f)) return A_FINISH;
         const float F = fresnel_dielectric(cif, n_i, n_t);
         const float4 u = path_draw(J, st.pix, (unsigned)st.s, (unsigned)st.cv, 0u, (unsigned)st.lam);
         if (u.x < F) {
             wi = scale(nn, RO::mulf(ci, 2.0f)) - wo;
-            if (dot3(tof3(wi), g) <= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            if (dot3(tof3(wi), g) <= 0.0f) return A_FINISH;
         } else {
             R eta = RO::f(n_i) / RO::f(n_t);
             R ct = RO::sqrt_(RO::f(1.0f) - eta * eta * (RO::f(1.0f) - ci * ci));
             wi = scale(nn, eta * ci - ct) - scale(wo, eta);
-            if (dot3(tof3(wi), g) >= 0.0f) return finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            if (dot3(tof3(wi), g) >= 0.0f) return A_FINISH;
             st.beta_c *= RO::to_f(eta * eta);
             st.n_cur = n_t;
         }
@@ -874,7 +887,7 @@ __device__ __forceinline__ int coherent_hit(Lane<R> &st, const HitF &hit, float 
     st.rd = tof3(wi);
     st.rskip = tri;
     st.rtmax = 1e30f;
-    return S_COH;
+    return A_COH;
 }
 
 // ------------------------------------------------------------------------------ the kernel
@@ -944,18 +957,30 @@ __global__ void __launch_bounds__(BLOCK) trace_kernel(const JobTable *__restrict
         if (STATS) { cnt.rays++; cnt.shadows += shadow; cnt.bounces += (st.state == S_BOUNCE); }
         const bool any = traverse<STATS>(st.J->sc, st.ro, st.rd, st.rtmax, st.rskip, coh ? 0.0f : WATERTIGHT_EPS, coh,
                                          shadow, hit, t_near, stk, status, cnt);
+        int act;
         if (coh) {
-            st.state = coherent_hit<R, STATS>(st, hit, t_near, acc, stk, status, cnt);
+            act = coherent_hit<R, STATS>(st, hit, t_near, stk, status, cnt);
         } else if (shadow) {
             if (!any) st.L += st.nee_val;
-            st.state = st.has_bounce ? take_bounce(st) : finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            act = A_FINISH;
+            if (st.has_bounce) {
+                take_bounce(st);
+                act = A_BOUNCE;
+            }
         } else if (hit.tri < 0) {
-            st.state = finish_sample<R, STATS>(st, acc, stk, status, cnt);
+            act = A_FINISH;
         } else {
             st.v++;
             st.t_prev = hit.t;
-            const Surf S = make_surf(st.J->sc, hit.tri, st.ro + st.rd * hit.t, hit.u, hit.v);
-            st.state = vertex<R, STATS>(st, S, -st.rd, acc, stk, status, cnt);
+            st.surf = make_surf(st.J->sc, hit.tri, st.ro + st.rd * hit.t, hit.u, hit.v);
+            st.wo = -st.rd;
+            act = A_VERTEX;
+        }
+        if (act == A_VERTEX) act = vertex(st);
+        if (act == A_FINISH) {
+            st.state = finish_sample<R, STATS>(st, acc, stk, status, cnt);
+        } else {
+            st.state = act == A_COH ? S_COH : (act == A_SHADOW ? S_SHADOW : S_BOUNCE);
         }
     }
     if (STATS) {

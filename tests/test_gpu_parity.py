@@ -173,8 +173,8 @@ def test_tiny_and_ragged_sizes(ctx, cfg0, W, H, spp, K):
 def test_invalid_arguments_are_rejected(ctx, cfg0, torch_cuda):
     from paper_2606_14173_gb300 import hpt
     sc, sid, _ = cfg0
-    out = hpt.alloc_output(S.config0_render())
-    bad = [dict(K=9), dict(spp=0), dict(max_depth=0), dict(lambdas=(20e-6,)), dict(W=0),
+    out = hpt.alloc_output(S.config0_render(K=8))
+    bad = [dict(K=9, W=128), dict(spp=0), dict(max_depth=0), dict(lambdas=(20e-6,)), dict(W=0),
            dict(T=np.diag([1.0, 2.0, 1.0, 1.0])), dict(facet_size=0.0)]
     for kw in bad:
         with pytest.raises(hpt.HptError) as e:
