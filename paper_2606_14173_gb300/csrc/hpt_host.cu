@@ -22,9 +22,13 @@
 #include "hpt_internal.h"
 
 namespace hpt {
-int trace_blocks_per_sm(int prec, bool stats);
-cudaError_t launch_trace(int prec, bool stats, const JobTable *d_table, SlotScratch *d_scratch, int grid,
-                         cudaStream_t s);
+cudaError_t wave_gen(int prec, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t);
+cudaError_t wave_trace(int prec, bool stats, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, int it,
+                       int grid, cudaStream_t);
+cudaError_t wave_shade(int prec, bool stats, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, int it,
+                       int grid, cudaStream_t);
+cudaError_t wave_accum(int prec, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t);
+int wave_occupancy(int prec, int which);
 }  // namespace hpt
 
 using namespace hpt;
@@ -201,7 +205,6 @@ struct SceneRec {
 
 struct Slot {
     JobTable *d_table = nullptr;
-    SlotScratch *d_scratch = nullptr;
     JobTable *h_table = nullptr;   // pinned
     cudaEvent_t done = nullptr;
     bool used = false;
@@ -224,7 +227,14 @@ struct Request {
 struct hpt_ctx {
     int device = 0;
     int sm_count = 0;
-    int bps[2] = {1, 1};
+    int grid_trace[2] = {1, 1}, grid_shade[2] = {1, 1};
+    // path state of one wave (capacity paths), all wave work runs on wstream
+    PathBufs pb{};
+    void *pb_arena = nullptr;
+    int capacity = 1 << 20;
+    SlotScratch *d_scr = nullptr;
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::mutex mu;
     std::map<uint64_t, std::unique_ptr<SceneRec>> scenes;
     uint64_t next_scene = 1;
@@ -279,8 +289,15 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     ctx->device = device;
     ctx->t0 = std::chrono::steady_clock::now();
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
-    ctx->bps[0] = trace_blocks_per_sm(0, false);
-    ctx->bps[1] = trace_blocks_per_sm(1, false);
+    for (int prec = 0; prec < 2; ++prec) {
+        ctx->grid_trace[prec] = ctx->sm_count * wave_occupancy(prec, 0);
+        ctx->grid_shade[prec] = ctx->sm_count * wave_occupancy(prec, 1);
+    }
+    CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
+    CUDA_TRY(cudaMemset(ctx->d_scr, 0, sizeof(SlotScratch)));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     // cos/sin(2 pi k / 256) split into float pairs for the double-float cone sampler
     float4 tab[256];
     for (int k = 0; k < 256; ++k) {
@@ -294,8 +311,6 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     for (int i = 0; i < hpt_ctx::NSLOTS; ++i) {
         Slot &s = ctx->slots[i];
         CUDA_TRY(cudaMalloc(&s.d_table, sizeof(JobTable)));
-        CUDA_TRY(cudaMalloc(&s.d_scratch, sizeof(SlotScratch)));
-        CUDA_TRY(cudaMemset(s.d_scratch, 0, sizeof(SlotScratch)));
         CUDA_TRY(cudaMallocHost(&s.h_table, sizeof(JobTable)));
         CUDA_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
     }
@@ -329,10 +344,14 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
     for (auto &s : ctx->slots) {
         cudaFree(s.d_table);
-        cudaFree(s.d_scratch);
         cudaFreeHost(s.h_table);
         cudaEventDestroy(s.done);
     }
+    if (ctx->pb_arena) cudaFree(ctx->pb_arena);
+    if (ctx->d_scr) cudaFree(ctx->d_scr);
+    if (ctx->wstream) cudaStreamDestroy(ctx->wstream);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
     if (ctx->d_sincos) cudaFree(ctx->d_sincos);
     if (ctx->sstream) cudaStreamDestroy(ctx->sstream);
@@ -741,29 +760,115 @@ static Slot *acquire_slot(hpt_ctx *ctx)
     return s;
 }
 
-// queue one persistent launch over 'jobs' on stream s
-static hpt_status launch_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t s,
-                              Slot **slot_out)
+// bytes of path state per path (see PathBufs)
+static size_t path_bytes() { return 7 * 8 + 3 * 4 + 4 + 6 * 4 + 3 * 16 + 16 + 4 + 3 * 4 + 3 * 4 + 6 * 4; }
+
+static hpt_status ensure_paths(hpt_ctx *ctx)
 {
+    if (ctx->pb_arena) return HPT_OK;
+    const size_t B = (size_t)ctx->capacity;
+    CUDA_TRY(cudaMalloc(&ctx->pb_arena, B * path_bytes() + 64 * 256));
+    char *p = (char *)ctx->pb_arena;
+    auto take = [&](size_t bytes) {
+        void *r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    PathBufs &b = ctx->pb;
+    for (int k = 0; k < 3; ++k) b.co[k] = take(8 * B);
+    for (int k = 0; k < 3; ++k) b.cd[k] = take(8 * B);
+    b.opl = take(8 * B);
+    b.ncur = (float *)take(4 * B);
+    b.betac = (float *)take(4 * B);
+    b.cost = (float *)take(4 * B);
+    b.cv = (int *)take(4 * B);
+    b.L = (float *)take(4 * B);
+    b.beta = (float *)take(4 * B);
+    b.ppdf = (float *)take(4 * B);
+    b.tprev = (float *)take(4 * B);
+    b.nee = (float *)take(4 * B);
+    b.vfl = (int *)take(4 * B);
+    b.ray_o = (float4 *)take(16 * B);
+    b.ray_d = (float4 *)take(16 * B);
+    b.sh_d = (float4 *)take(16 * B);
+    b.hit = (float4 *)take(16 * B);
+    b.occl = (int *)take(4 * B);
+    b.amp = (float *)take(4 * B);
+    b.fturn = (float *)take(4 * B);
+    b.basep = (float *)take(4 * B);
+    b.cx = (int *)take(4 * B);
+    b.cy = (int *)take(4 * B);
+    b.cz = (int *)take(4 * B);
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 2; ++j) b.q[k][j] = (int *)take(4 * B);
+    b.capacity = (int)B;
+    return HPT_OK;
+}
+
+// One launch group: the waves covering all items of 'jobs', queued on the context's wave
+// stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
+static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t user)
+{
+    hpt_status st = ensure_paths(ctx);
+    if (st) return st;
     Slot *slot = acquire_slot(ctx);
     JobTable *h = slot->h_table;
     h->n_jobs = n;
-    long long items = 0;
-    for (int i = 0; i < n; ++i) {
-        h->jobs[i] = jobs[i];
-        h->jobs[i].item_start = items;
-        items += jobs[i].n_items;
+    for (int i = 0; i < n; ++i) h->jobs[i] = jobs[i];
+    cudaStream_t ws = ctx->wstream;
+    CUDA_TRY(cudaEventRecord(ctx->ev_in, user));
+    CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
+    const size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
+    CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, ws));
+    if (stats) CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
+    const JobTable *jt = slot->d_table;
+    const int B = ctx->capacity;
+    WaveDesc wd;
+    memset(&wd, 0, sizeof wd);
+    int max_depth = 1;
+    auto flush = [&]() -> hpt_status {
+        if (wd.n_seg == 0) return HPT_OK;
+        const int n_iter = max_depth + 1;
+        CUDA_TRY(cudaMemsetAsync(ctx->d_scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws));
+        CUDA_TRY(wave_gen(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        for (int it = 0; it < n_iter; ++it) {
+            CUDA_TRY(wave_trace(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_trace[prec], ws));
+            CUDA_TRY(wave_shade(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws));
+        }
+        CUDA_TRY(wave_accum(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        memset(&wd, 0, sizeof wd);
+        max_depth = 1;
+        return HPT_OK;
+    };
+    for (int j = 0; j < n; ++j) {
+        const int spp = jobs[j].spp;
+        if (spp > B) return fail(HPT_ERR_UNSUPPORTED, "spp %d exceeds the wave capacity %d", spp, B);
+        long long c = 0;
+        while (c < jobs[j].n_items) {
+            int cap = (B - wd.n_paths) / spp;
+            if (cap <= 0 || wd.n_seg == MAX_SEG) {
+                st = flush();
+                if (st) return st;
+                continue;
+            }
+            const int take = (int)std::min<long long>(jobs[j].n_items - c, cap);
+            WaveSeg &g = wd.seg[wd.n_seg++];
+            g.job = j;
+            g.spp = spp;
+            g.item_begin = c;
+            g.item_count = take;
+            g.path_offset = wd.n_paths;
+            wd.n_paths += take * spp;
+            wd.n_items += take;
+            max_depth = std::max(max_depth, jobs[j].max_depth);
+            c += take;
+        }
     }
-    h->total_items = items;
-    size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
-    CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(&slot->d_scratch->next_item, 0, sizeof(unsigned long long), s));
-    if (stats) CUDA_TRY(cudaMemsetAsync(slot->d_scratch->counters, 0, sizeof(slot->d_scratch->counters), s));
-    long long max_grid = (items + BLOCK - 1) / BLOCK;
-    int grid = (int)std::min<long long>((long long)ctx->sm_count * ctx->bps[prec], std::max<long long>(max_grid, 1));
-    CUDA_TRY(launch_trace(prec, stats, slot->d_table, slot->d_scratch, grid, s));
-    CUDA_TRY(cudaEventRecord(slot->done, s));
-    if (slot_out) *slot_out = slot;
+    st = flush();
+    if (st) return st;
+    CUDA_TRY(cudaEventRecord(slot->done, ws));
+    CUDA_TRY(cudaEventRecord(ctx->ev_out, ws));
+    CUDA_TRY(cudaStreamWaitEvent(user, ctx->ev_out, 0));
     return HPT_OK;
 }
 
@@ -778,7 +883,7 @@ extern "C" hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_rende
     st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    return launch_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream, nullptr);
+    return run_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream);
 }
 
 extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_host,
@@ -804,7 +909,7 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
     }
     J.out = (float2 *)ctx->host_out_dev;
     cudaStream_t s = (cudaStream_t)stream;
-    st = launch_jobs(ctx, &J, 1, desc->precision, false, s, nullptr);
+    st = run_jobs(ctx, &J, 1, desc->precision, false, s);
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out_dev, need, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -814,17 +919,12 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
 static hpt_status read_status(hpt_ctx *ctx)
 {
     unsigned bits = 0;
-    for (auto &s : ctx->slots) {
-        unsigned v = 0;
-        CUDA_TRY(cudaMemcpy(&v, &s.d_scratch->status, sizeof v, cudaMemcpyDeviceToHost));
-        if (v) {
-            bits |= v;
-            CUDA_TRY(cudaMemset(&s.d_scratch->status, 0, sizeof v));
-        }
-    }
-    if (bits)
+    CUDA_TRY(cudaMemcpy(&bits, &ctx->d_scr->status, sizeof bits, cudaMemcpyDeviceToHost));
+    if (bits) {
+        CUDA_TRY(cudaMemset(&ctx->d_scr->status, 0, sizeof bits));
         return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
                     (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
+    }
     return HPT_OK;
 }
 
@@ -849,13 +949,13 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
     st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    Slot *slot = nullptr;
-    st = launch_jobs(ctx, &J, 1, desc->precision, true, 0, &slot);
+    st = run_jobs(ctx, &J, 1, desc->precision, true, 0);
     if (st) return st;
     CUDA_TRY(cudaStreamSynchronize(0));
     unsigned long long c[8];
-    CUDA_TRY(cudaMemcpy(c, slot->d_scratch->counters, sizeof c, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(c, ctx->d_scr->counters, sizeof c, cudaMemcpyDeviceToHost));
     for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k];
+    counters[0] = (uint64_t)desc->n_lambda * desc->W * (uint64_t)desc->H * desc->spp;   // path samples
     return read_status(ctx);
 }
 

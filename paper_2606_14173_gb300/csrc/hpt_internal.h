@@ -5,10 +5,15 @@
 
 namespace hpt {
 
-constexpr int KMAX = 8;            // holograms per path set held by one thread
-constexpr int BLOCK = 128;         // threads per block of the trace kernel
-constexpr int STACK = 64;          // traversal stack entries per thread (shared memory)
-constexpr int MAX_JOBS = 64;       // jobs (requests) in one persistent launch
+constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
+constexpr int TSTACK = 48;         // traversal stack entries per thread (shared memory)
+constexpr int TRACE_BLOCK = 128;   // threads per block of the trace kernel
+constexpr int SHADE_BLOCK = 128;
+constexpr int GEN_BLOCK = 256;
+constexpr int ACCUM_BLOCK = 128;
+constexpr int MAX_JOBS = 64;       // jobs (requests) of one launch group
+constexpr int MAX_SEG = 16;        // job segments of one wave
+constexpr int MAX_ITER = 66;       // trace/shade iterations of a wave: max_depth + 1 <= 65
 constexpr int TILE_W = 8, TILE_H = 4;
 
 // status bits written by the kernels
@@ -64,7 +69,6 @@ struct DevScene {
 struct DevJob {
     DevScene sc;
     float2 *out;                // [n_lambda][K][H][W]
-    long long item_start;       // first global work item of this job
     long long n_items;          // n_lambda * n_tiles * 32
     int W, H, n_lambda, spp, max_depth, K, hologram_offset, phase_mode, use_cache;
     int t_identity;
@@ -86,16 +90,51 @@ struct DevJob {
 
 struct JobTable {
     int n_jobs;
-    long long total_items;
+    int pad;
     DevJob jobs[MAX_JOBS];
+};
+
+// A wave: consecutive work items of up to MAX_SEG jobs, with all their samples.  Path p of a
+// segment with n items is sample s = (p - path_offset) / n of item item_begin + (p - path_offset) % n.
+struct WaveSeg {
+    int job;
+    int spp;
+    long long item_begin;
+    int item_count;
+    int path_offset;
+};
+
+struct WaveDesc {
+    int n_seg;
+    int n_paths;
+    int n_items;
+    int pad;
+    WaveSeg seg[MAX_SEG];
+};
+
+// Structure-of-arrays state of the paths of one wave (capacity paths each).  The coherent
+// quantities are 8-byte slots holding a double or a double-float (hi, lo) pair.
+struct PathBufs {
+    void *co[3], *cd[3], *opl;           // coherent origin, direction, optical path length
+    float *ncur, *betac, *cost;          // medium index, delta-chain throughput, cos(theta) of the sample
+    int *cv;                             // coherent vertex count
+    float *L, *beta, *ppdf, *tprev, *nee;
+    int *vfl;                            // incoherent vertex | flags
+    float4 *ray_o, *ray_d, *sh_d;        // float ray (origin | tmax, direction | skip), shadow direction | tmax
+    float4 *hit;                         // t, u, v, triangle
+    int *occl;                           // shadow ray blocked
+    float *amp, *fturn, *basep;          // sample record: amplitude factor, frac(r / lambda), estimator weight
+    int *cx, *cy, *cz;                   // facet cell of the real image point
+    int *q[3][2];                        // queues (coherent, incoherent, shadow) x ping-pong
+    int capacity;
 };
 
 // device-side scratch of one launch slot
 struct SlotScratch {
-    unsigned long long next_item;   // work counter (reset before every launch)
     unsigned int status;            // error bits (sticky until read by hpt_sync)
     unsigned int pad;
     unsigned long long counters[8];
+    int qcount[MAX_ITER + 1][3];    // queue lengths per iteration
 };
 
 }  // namespace hpt

@@ -1,40 +1,40 @@
-// Dispatch over the trace-kernel variants (one translation unit per variant).
+// Dispatch of the wavefront kernels over the two coherent arithmetics (FP64 = 0, DF32 = 1);
+// each arithmetic lives in its own translation unit so that they compile in parallel.
 #include <cuda_runtime.h>
 #include "hpt_internal.h"
 
 namespace hpt {
-const void *kernel_f64();
-const void *kernel_f64_stats();
-const void *kernel_df();
-const void *kernel_df_stats();
-void launch_f64(const JobTable *, SlotScratch *, int, cudaStream_t);
-void launch_f64_stats(const JobTable *, SlotScratch *, int, cudaStream_t);
-void launch_df(const JobTable *, SlotScratch *, int, cudaStream_t);
-void launch_df_stats(const JobTable *, SlotScratch *, int, cudaStream_t);
+#define HPT_DECL(n)                                                                                              \
+    cudaError_t wave_gen_##n(const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t);  \
+    cudaError_t wave_trace_##n(bool, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, int, int, \
+                               cudaStream_t);                                                                    \
+    cudaError_t wave_shade_##n(bool, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, int, int, \
+                               cudaStream_t);                                                                    \
+    cudaError_t wave_accum_##n(const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t); \
+    int wave_occupancy_##n(int);
+HPT_DECL(f64)
+HPT_DECL(df)
+#undef HPT_DECL
 
-static const void *kernel_ptr(int prec, bool stats)
+cudaError_t wave_gen(int prec, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                     cudaStream_t s)
 {
-    if (prec == 0) return stats ? kernel_f64_stats() : kernel_f64();
-    return stats ? kernel_df_stats() : kernel_df();
+    return prec == 0 ? wave_gen_f64(jt, wd, pb, scr, s) : wave_gen_df(jt, wd, pb, scr, s);
 }
-
-int trace_blocks_per_sm(int prec, bool stats)
+cudaError_t wave_trace(int prec, bool st, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                       int it, int grid, cudaStream_t s)
 {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_ptr(prec, stats), BLOCK, 0) != cudaSuccess) return 1;
-    return nb > 0 ? nb : 1;
+    return prec == 0 ? wave_trace_f64(st, jt, wd, pb, scr, it, grid, s) : wave_trace_df(st, jt, wd, pb, scr, it, grid, s);
 }
-
-cudaError_t launch_trace(int prec, bool stats, const JobTable *d_table, SlotScratch *d_scratch, int grid,
-                         cudaStream_t s)
+cudaError_t wave_shade(int prec, bool st, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                       int it, int grid, cudaStream_t s)
 {
-    if (prec == 0) {
-        if (stats) launch_f64_stats(d_table, d_scratch, grid, s);
-        else launch_f64(d_table, d_scratch, grid, s);
-    } else {
-        if (stats) launch_df_stats(d_table, d_scratch, grid, s);
-        else launch_df(d_table, d_scratch, grid, s);
-    }
-    return cudaGetLastError();
+    return prec == 0 ? wave_shade_f64(st, jt, wd, pb, scr, it, grid, s) : wave_shade_df(st, jt, wd, pb, scr, it, grid, s);
 }
+cudaError_t wave_accum(int prec, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                       cudaStream_t s)
+{
+    return prec == 0 ? wave_accum_f64(jt, wd, pb, scr, s) : wave_accum_df(jt, wd, pb, scr, s);
+}
+int wave_occupancy(int prec, int which) { return prec == 0 ? wave_occupancy_f64(which) : wave_occupancy_df(which); }
 }  // namespace hpt

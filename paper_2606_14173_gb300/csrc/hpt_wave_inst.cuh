@@ -1,0 +1,45 @@
+// Host-side launchers of the wavefront kernels for one coherent arithmetic R.
+#pragma once
+#include "hpt_wave.cuh"
+
+namespace hpt {
+
+template <class R> struct WaveLaunch {
+    static cudaError_t gen(const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr, cudaStream_t s)
+    {
+        const int g = (wd.n_paths + GEN_BLOCK - 1) / GEN_BLOCK;
+        if (g > 0) k_gen<R><<<g, GEN_BLOCK, 0, s>>>(jt, wd, pb, scr);
+        return cudaGetLastError();
+    }
+    static cudaError_t trace(bool stats, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                             int it, int grid, cudaStream_t s)
+    {
+        if (stats) k_trace<R, true><<<grid, TRACE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        else k_trace<R, false><<<grid, TRACE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        return cudaGetLastError();
+    }
+    static cudaError_t shade(bool stats, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
+                             int it, int grid, cudaStream_t s)
+    {
+        if (stats) k_shade<R, true><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        else k_shade<R, false><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        return cudaGetLastError();
+    }
+    static cudaError_t accum(const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr, cudaStream_t s)
+    {
+        const int g = (wd.n_items + ACCUM_BLOCK - 1) / ACCUM_BLOCK;
+        if (g > 0) k_accum<R><<<g, ACCUM_BLOCK, 0, s>>>(jt, wd, pb, scr);
+        return cudaGetLastError();
+    }
+    // resident blocks per SM of the trace (0) and shade (1) kernels
+    static int occupancy(int which)
+    {
+        int nb = 0;
+        cudaError_t e = which == 0
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace<R, false>, TRACE_BLOCK, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<R, false>, SHADE_BLOCK, 0);
+        return (e == cudaSuccess && nb > 0) ? nb : 1;
+    }
+};
+
+}  // namespace hpt
