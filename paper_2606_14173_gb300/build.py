@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = _nvcc()
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                    "-I", CSRC]
+                    "-I", CSRC] + os.environ.get("HPT_NVCC_FLAGS", "").split()
     objs = []
 
     def comp(src):

@@ -80,16 +80,35 @@ struct HitF {
     int tri;
 };
 
+// Triangles whose float test was within its error band (near an edge, or tied in distance):
+// the closest hit among them is re-decided in the coherent arithmetic.
+constexpr int NCAND = 4;
+struct Cands {
+    float t[NCAND];
+    int id[NCAND];
+    int n;          // > NCAND: overflow
+    __device__ __forceinline__ void add(float tt, int i)
+    {
+        for (int k = 0; k < NCAND; ++k)
+            if (k < n && id[k] == i) return;
+        if (n < NCAND) {
+            t[n] = tt;
+            id[n] = i;
+        }
+        ++n;
+    }
+};
+
 struct Counters {
     unsigned rays, boxes, tris, refines, fallbacks, shadows, bounces, samples;
 };
 
-// Closest (or any) hit of a float ray against the BVH.  TRACK: record in t_near the smallest
-// distance of a triangle met within NEAR_MARGIN of an edge, or of two hits tied within TIE_REL,
-// so that the caller can re-decide the hit in double precision.
+// Closest (or any) hit of a float ray against the BVH.  TRACK: collect the triangles met within
+// NEAR_MARGIN of an edge, or tied in distance within TIE_REL, no farther than the float winner,
+// so that the caller can re-decide the hit in the coherent arithmetic.
 template <bool STATS, int SSTRIDE>
 __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d, float tmax, int skip, float eps_w,
-                                         bool TRACK, bool ANYHIT, HitF &h, float &t_near, int *stk, int &status,
+                                         bool TRACK, bool ANYHIT, HitF &h, Cands &cand, int *stk, int &status,
                                          Counters &cnt)
 {
     const float big = 1e30f;
@@ -100,7 +119,8 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     h.t = tmax;
     h.tri = -1;
     h.u = h.v = 0.0f;
-    if (TRACK) t_near = big;
+    (void)big;
+    if (TRACK) cand.n = 0;
     const float cull = TRACK ? (1.0f + 4.0f * TIE_REL) : 1.0f;
     const float4 *__restrict__ nodes = sc.nodes;
     const float4 *__restrict__ tris = sc.tri4;
@@ -157,8 +177,8 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
             float v = dot3(d, qv) * idet;
             float t = dot3(e2, qv) * idet;
             if (TRACK) {
-                float m = fminf(fminf(u, v), 1.0f - u - v);
-                if (fabsf(m) < NEAR_MARGIN && t > 0.0f && t < t_near) t_near = t;
+                const float m = fminf(fminf(u, v), 1.0f - u - v);
+                if (fabsf(m) < NEAR_MARGIN && t > 0.0f && t <= h.t * (1.0f + 10.0f * TIE_REL)) cand.add(t, id);
             }
             bool inside = (u >= -eps_w) && (v >= -eps_w) && (u + v <= 1.0f + eps_w) && (t > 0.0f);
             if (!inside) continue;
@@ -166,7 +186,10 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
                 if (t < tmax) { h.t = t; h.tri = id; return true; }
                 continue;
             }
-            if (TRACK && h.tri >= 0 && fabsf(t - h.t) <= TIE_REL * h.t) t_near = fminf(t_near, fmaxf(t, h.t));
+            if (TRACK && h.tri >= 0 && fabsf(t - h.t) <= TIE_REL * h.t) {
+                cand.add(h.t, h.tri);
+                cand.add(t, id);
+            }
             if (t < h.t || (t == h.t && id < h.tri)) {
                 h.t = t; h.u = u; h.v = v; h.tri = id;
             }

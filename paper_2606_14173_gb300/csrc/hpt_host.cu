@@ -7,6 +7,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -232,6 +233,7 @@ struct hpt_ctx {
     PathBufs pb{};
     void *pb_arena = nullptr;
     int capacity = 1 << 20;
+    int debug_waves = 0;
     SlotScratch *d_scr = nullptr;
     cudaStream_t wstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -293,6 +295,8 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
         ctx->grid_trace[prec] = ctx->sm_count * wave_occupancy(prec, 0);
         ctx->grid_shade[prec] = ctx->sm_count * wave_occupancy(prec, 1);
     }
+    if (const char *e = getenv("HPT_WAVE_PATHS")) ctx->capacity = std::max(1 << 12, std::min(atoi(e), 1 << 26));
+    if (const char *e = getenv("HPT_DEBUG_WAVES")) ctx->debug_waves = atoi(e);
     CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
     CUDA_TRY(cudaMemset(ctx->d_scr, 0, sizeof(SlotScratch)));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
@@ -836,6 +840,16 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
             CUDA_TRY(wave_shade(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws));
         }
         CUDA_TRY(wave_accum(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        if (ctx->debug_waves > 0) {
+            // diagnostic: queue lengths per iteration of the first waves (HPT_DEBUG_WAVES=n)
+            --ctx->debug_waves;
+            int q[MAX_ITER + 1][3];
+            CUDA_TRY(cudaStreamSynchronize(ws));
+            CUDA_TRY(cudaMemcpy(q, ctx->d_scr->qcount, sizeof(int) * 3 * (n_iter + 1), cudaMemcpyDeviceToHost));
+            fprintf(stderr, "wave paths=%d items=%d:", wd.n_paths, wd.n_items);
+            for (int it = 0; it <= n_iter; ++it) fprintf(stderr, " [%d|%d|%d]", q[it][0], q[it][1], q[it][2]);
+            fprintf(stderr, "\n");
+        }
         memset(&wd, 0, sizeof wd);
         max_depth = 1;
         return HPT_OK;

@@ -6,8 +6,9 @@
 //   k_gen                 s1, s2: pixel centre and a direction in the SLM cone, to world space
 //   (k_trace, k_shade) x (max_depth + 1)
 //     k_trace             s3: closest hit of coherent and incoherent rays, any hit of shadow rays
-//                         (float BVH; the coherent hit is re-decided in double when the float
-//                         test was within its error band of an edge or a tie)
+//                         (float BVH; when the float test of a coherent ray was within its error
+//                         band of an edge or a tie, the hit is re-decided among the candidates in
+//                         the coherent arithmetic)
 //     k_shade             s3-s5: coherent refinement and delta lobes (R arithmetic), the real
 //                         image point P, incoherent vertices with NEE and BSDF sampling (Eq. 1)
 //   k_accum               s6-s9: per pixel and wavelength, the K facet phases and the
@@ -153,6 +154,35 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
 }
 
 // ------------------------------------------------------------------------------------ s3
+template <class R> __device__ __forceinline__ bool r_less(R a, R b);
+template <> __device__ __forceinline__ bool r_less<double>(double a, double b) { return a < b; }
+template <> __device__ __forceinline__ bool r_less<df>(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+template <class R> __device__ __forceinline__ bool r_nonneg(R a);
+template <> __device__ __forceinline__ bool r_nonneg<double>(double a) { return a >= 0.0; }
+template <> __device__ __forceinline__ bool r_nonneg<df>(df a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo >= 0.0f); }
+
+// Plane intersection and barycentric inside test of one triangle in the coherent arithmetic
+// (the decision rule of the definition: closed triangle, distance beyond tmin).
+template <class R>
+__device__ __forceinline__ bool exact_hit(const DevScene &sc, int tri, const R3<R> &co, const R3<R> &cd, R tmin, R &t)
+{
+    using RO = RealOps<R>;
+    const int rb = tri * REF_N;
+    const R3<R> n = r3<R>(RO::load(sc.ref64, sc.refdf, rb), RO::load(sc.ref64, sc.refdf, rb + 1),
+                          RO::load(sc.ref64, sc.refdf, rb + 2));
+    const R den = rdot(n, cd);
+    if (RO::to_f(den) == 0.0f) return false;
+    t = (RO::load(sc.ref64, sc.refdf, rb + 3) - rdot(n, co)) / den;
+    if (!r_less<R>(tmin, t)) return false;
+    const uint4 ix = __ldg(sc.tri_attr + tri);
+    const R3<R> dP = (co + scale(cd, t)) - fromf3<R>(f3(sc.verts[3 * ix.x], sc.verts[3 * ix.x + 1], sc.verts[3 * ix.x + 2]));
+    const R b1 = rdot(r3<R>(RO::load(sc.ref64, sc.refdf, rb + 4), RO::load(sc.ref64, sc.refdf, rb + 5),
+                            RO::load(sc.ref64, sc.refdf, rb + 6)), dP);
+    const R b2 = rdot(r3<R>(RO::load(sc.ref64, sc.refdf, rb + 7), RO::load(sc.ref64, sc.refdf, rb + 8),
+                            RO::load(sc.ref64, sc.refdf, rb + 9)), dP);
+    return r_nonneg<R>(b1) && r_nonneg<R>(b2) && r_nonneg<R>(RO::f(1.0f) - b1 - b2);
+}
+
 template <class R, bool STATS>
 __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
                                                        SlotScratch *__restrict__ scr, int it)
@@ -177,31 +207,53 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(const JobTable *__restric
         const float4 o4 = pb.ray_o[p], d4 = pb.ray_d[p];
         const int skip = __float_as_int(d4.w);
         HitF h;
-        float tn = 1e30f;
+        Cands cand;
         if (STATS) cnt.rays++;
         if (kind == 2) {
             if (STATS) cnt.shadows++;
             const float4 s4 = pb.sh_d[p];
             const bool any = traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(s4), s4.w, skip, WATERTIGHT_EPS, false, true, h,
-                                                          tn, stk, status, cnt);
+                                                          cand, stk, status, cnt);
             pb.occl[p] = any ? 1 : 0;
         } else if (kind == 1) {
             if (STATS) cnt.bounces++;
-            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, WATERTIGHT_EPS, false, false, h, tn, stk, status,
-                                         cnt);
+            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, WATERTIGHT_EPS, false, false, h, cand, stk,
+                                         status, cnt);
             pb.hit[p] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
         } else {
-            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, 0.0f, true, false, h, tn, stk, status, cnt);
+            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, 0.0f, true, false, h, cand, stk, status, cnt);
             int tri = h.tri;
-            if (tn < 1e29f && (tri < 0 || tn <= h.t * (1.0f + 10.0f * TIE_REL))) {
-                // the float test was within its error band: decide the hit in double precision
-                if (STATS) cnt.fallbacks++;
-                double tt;
-                tri = traverse_fp64<TRACE_BLOCK>(
-                    sc, RO::to_d(RS<R>::ld(pb.co[0], p)), RO::to_d(RS<R>::ld(pb.co[1], p)),
-                    RO::to_d(RS<R>::ld(pb.co[2], p)), RO::to_d(RS<R>::ld(pb.cd[0], p)), RO::to_d(RS<R>::ld(pb.cd[1], p)),
-                    RO::to_d(RS<R>::ld(pb.cd[2], p)), pb.cv[p] > 0 ? COH_TMIN : 0.0, skip, &tt, stk, status);
-                h.t = (float)tt;
+            if (cand.n > 0) {
+                // the float test was within its error band: decide among the candidates (and the
+                // float winner) in the coherent arithmetic; a full double traversal only when the
+                // list overflowed or no candidate holds
+                if (STATS) cnt.refines++;
+                const R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
+                const R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
+                const R tmin = pb.cv[p] > 0 ? RO::fromd(COH_TMIN) : RO::f(0.0f);
+                int best = -1;
+                R bt = RO::f(0.0f);
+                if (cand.n <= NCAND) {
+                    for (int k = -1; k < cand.n; ++k) {
+                        const int id = k < 0 ? h.tri : cand.id[k];
+                        if (id < 0 || id == skip) continue;
+                        R tk;
+                        if (exact_hit<R>(sc, id, co, cd, tmin, tk) &&
+                            (best < 0 || r_less<R>(tk, bt) || (!r_less<R>(bt, tk) && id < best))) {
+                            best = id;
+                            bt = tk;
+                        }
+                    }
+                }
+                if (best >= 0) {
+                    tri = best;
+                } else {
+                    if (STATS) cnt.fallbacks++;
+                    double tt;
+                    tri = traverse_fp64<TRACE_BLOCK>(sc, RO::to_d(co.x), RO::to_d(co.y), RO::to_d(co.z), RO::to_d(cd.x),
+                                                     RO::to_d(cd.y), RO::to_d(cd.z), pb.cv[p] > 0 ? COH_TMIN : 0.0, skip,
+                                                     &tt, stk, status);
+                }
             }
             pb.hit[p] = make_float4(h.t, 0.0f, 0.0f, __int_as_float(tri));
         }
@@ -399,7 +451,6 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
         if (coh) {
             const int tri = __float_as_int(pb.hit[p].w);
             if (tri >= 0) {
-                if (STATS) cnt.refines++;
                 R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
                 R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
                 R opl = RS<R>::ld(pb.opl, p);
@@ -596,10 +647,10 @@ __device__ __noinline__ float2 point_field(const DevJob *Jp, int lam, int px, in
         const float3 dw = tof3(pw - O);
         const float dist = sqrtf(dot3(dw, dw));
         HitF h;
-        float tn;
+        Cands cand;
         Counters dummy;
         if (traverse<false, ACCUM_BLOCK>(sc, Of, dw * (1.0f / dist), dist * (1.0f - SHADOW_SHRINK), -1, WATERTIGHT_EPS,
-                                         false, true, h, tn, stk, status, dummy))
+                                         false, true, h, cand, stk, status, dummy))
             continue;
         const float turns = RO::frac_f(r * RO::rc(J.inv_lambda[lam]));
         float sn, cs;
