@@ -232,7 +232,7 @@ struct hpt_ctx {
     // path state of one wave (capacity paths), all wave work runs on wstream
     PathBufs pb{};
     void *pb_arena = nullptr;
-    int capacity = 1 << 20;
+    int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
     SlotScratch *d_scr = nullptr;
     cudaStream_t wstream = nullptr;
