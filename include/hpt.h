@@ -195,6 +195,34 @@ hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_ms);
  * t[0] submitted, t[1] admitted (launched), t[2] completed. */
 hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[3]);
 
+/* ---- trace with fixed scratch: an entry point that allocates nothing -------------------
+ * The paper has no counterpart; this is an interface for callers that cannot allocate device
+ * memory while they run -- for instance a real-time hologram display loop that must not stall
+ * on the device-wide synchronisation that cudaMalloc / cudaFree can cause, or a host process
+ * whose device memory is handed out up front by another framework's pool, so that a driver
+ * allocation in the middle of serving could fail.
+ *
+ * hpt_trace_fixed_scratch computes exactly what hpt_trace computes (same inputs, same output
+ * layout, bitwise the same fields) but takes every scratch buffer of the trace -- the path
+ * state of a wave, the ray queues and their counters, the device copy of the render job --
+ * from one device array of HPT_FIXED_SCRATCH_BYTES (64 MiB) that the library defines at file
+ * scope; every GPU that loads the library holds that array until the process exits.  The call
+ * issues no cudaMalloc, cudaFree or other allocating routine.  The context, the uploaded
+ * scene (device memory allocated earlier by hpt_create / hpt_scene_upload) and out_dev
+ * (caller-owned, complex64 [n_lambda][K][H][W], out_bytes >= 8 n_lambda K H W) are its inputs
+ * and output.  The work is queued asynchronously on cuda_stream.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Frames of any size are split into waves that fit the array; spp larger than the array's
+ *    path capacity (about 300k paths) is rejected with HPT_ERR_INVALID_ARG.
+ *  - All calls share the one array and it keeps the last call's contents; the call clears what
+ *    must start at zero.  Calls whose work overlaps on the GPU (on different streams, or from
+ *    different contexts on one device) race on the array: serialise them on one stream.
+ *  - Device-side status bits of this entry point are not reported by hpt_sync.            */
+#define HPT_FIXED_SCRATCH_BYTES (64u << 20)
+hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                                   void *out_dev, size_t out_bytes, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

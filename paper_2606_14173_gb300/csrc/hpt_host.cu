@@ -986,3 +986,20 @@ extern "C" hpt_status hpt_request_times(hpt_ctx *, uint64_t, double *)
 {
     return fail(HPT_ERR_UNSUPPORTED, "serving not built yet");
 }
+
+// ------------------------------------------------------------ accessors for hpt_static.cu
+namespace hpt {
+hpt_status internal_make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out, size_t out_bytes,
+                             DevJob &J)
+{
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    return make_job(ctx, scene_id, desc, out, out_bytes, J, nullptr);
+}
+int internal_ctx_device(const hpt_ctx *ctx) { return ctx->device; }
+int internal_grid(const hpt_ctx *ctx, int prec, int which)
+{
+    return which == 0 ? ctx->grid_trace[prec] : ctx->grid_shade[prec];
+}
+hpt_status internal_fail(hpt_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace hpt

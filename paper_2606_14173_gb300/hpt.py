@@ -24,7 +24,7 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 # exported symbols, as declared in include/hpt.h
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
-           "hpt_request_times"]
+           "hpt_request_times", "hpt_trace_fixed_scratch"]
 
 
 class HptError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
     lib.hpt_wait.argtypes = [vp, C.c_uint64, C.c_uint32]
     lib.hpt_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double)]
+    lib.hpt_trace_fixed_scratch.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("hpt_destroy", "hpt_last_error"):
@@ -210,6 +211,14 @@ class Context:
         d = render_desc(r, precision)
         _check(self.lib.hpt_trace_host(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(out_host.ctypes.data),
                                        out_host.nbytes, _stream_ptr(stream)))
+
+    def trace_fixed_scratch(self, sid: int, r, out, precision=PREC_DF32, stream=None):
+        """hpt_trace_fixed_scratch: the same trace, with all scratch in the library's fixed
+        64 MiB device array; the call allocates no device memory."""
+        ptr, nbytes = _dev_buffer(out, r)
+        d = render_desc(r, precision)
+        _check(self.lib.hpt_trace_fixed_scratch(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes,
+                                                _stream_ptr(stream)))
 
     def trace_counters(self, sid: int, r, out, precision=PREC_DF32):
         ptr, nbytes = _dev_buffer(out, r)
