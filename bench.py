@@ -37,6 +37,15 @@ ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
 
 
+# name -> (description, render overrides of the 1080p RGB K=8 headline render)
+WORKLOADS = {
+    "cfg2": ("cfg2: 30-icosphere scene (~24k tris, Lambert/GGX/mirror/dielectric, 1 area light), 1920x1080 SLM 6.4 um, "
+             "RGB 638/520/450 nm, 64 spp, depth 4, K=8", {}),
+    "band": ("profiling case: the cfg2 scene and SLM pitch, a 1920x270 band at mid height, RGB, 16 spp, depth 4, K=8",
+             {"H": 270, "spp": 16}),
+}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -45,6 +54,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-counters", action="store_true")
+    p.add_argument("--workload", default="cfg2", choices=list(WORKLOADS),
+                   help="cfg2 = the headline workload; the others are smaller cases of the same kernels for profiling")
     return p.parse_args()
 
 
@@ -185,16 +198,21 @@ def main():
     ctx = hpt.Context(local)
     sc = S.config1_scene()
     sid = ctx.upload_scene(sc)
-    r = S.config2_render(seed=1 + rank)
+    wl_desc, wl_over = WORKLOADS[args.workload]
+    r = S.config2_render(seed=1 + rank, **wl_over)
     samples_per_step = r.path_samples()
     out = hpt.alloc_output(r)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
-    stream = torch.cuda.current_stream()
+    # all work on one dedicated stream: the legacy default stream serialises with the library's
+    # wave stream and would add idle time between steps
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def step_mixed():
         ctx.trace(sid, r, out, precision=hpt.PREC_DF32, stream=stream)
 
-    r_plain = [S.config2_render(seed=1 + rank, lambdas=(l,), channels=(c,)) for l, c in zip(r.lambdas, r.channels)]
+    r_plain = [S.config2_render(seed=1 + rank, lambdas=(l,), channels=(c,), **wl_over)
+               for l, c in zip(r.lambdas, r.channels)]
     outs_plain = [hpt.alloc_output(rp) for rp in r_plain]
 
     def step_plain():
@@ -241,23 +259,28 @@ def main():
                  "form": "FP64 coherent arithmetic, one launch per wavelength (3 per step), K=8 path reuse"}
 
     # end to end through the public API with host memory: result copied to pinned host memory
-    host = torch.empty(tuple(out.shape), dtype=torch.complex64, pin_memory=True).numpy()
-    for _ in range(max(1, args.warmup)):
-        ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
-    barrier(world)
-    t0 = time.perf_counter()
-    k_e2e = max(2, args.steps // 2)
-    for _ in range(k_e2e):
-        ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
-    e2e_s = allreduce_max(time.perf_counter() - t0, world)
-    import ctypes
-    h2d = ctypes.sizeof(hpt.RenderDesc) + 16 + 8 * 0   # render descriptor marshalled per call
-    e2e = {"value": world * samples_per_step * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(host.nbytes),
-           "api": "hpt_trace_host (device trace + D2H copy of all K x 3 fields into pinned host memory)"}
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(tuple(out.shape), dtype=torch.complex64, pin_memory=True).numpy()
+        for _ in range(max(1, args.warmup)):
+            ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        k_e2e = max(2, args.steps // 2)
+        for _ in range(k_e2e):
+            ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
+        e2e_s = allreduce_max(time.perf_counter() - t0, world)
+        import ctypes
+        h2d = ctypes.sizeof(hpt.RenderDesc)   # the render descriptor, copied to the device per call
+        e2e = {"value": world * samples_per_step * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(host.nbytes),
+               "api": "hpt_trace_host (device trace + D2H copy of all K x 3 fields into pinned host memory)"}
 
     # roofline of the trace kernel: algorithmic FP32 work from the per-sample work counters
-    cnt = ctx.trace_counters(sid, r, out, precision=hpt.PREC_DF32)
+    if args.no_counters:
+        cnt = {"samples": 1, "box_tests": 0, "tri_tests": 0, "refines": 0, "shadow_rays": 0, "bounces": 0}
+    else:
+        cnt = ctx.trace_counters(sid, r, out, precision=hpt.PREC_DF32)
     ns = max(cnt["samples"], 1)
     vertices = cnt["shadow_rays"] + cnt["bounces"] + cnt["refines"]
     flops = (cnt["box_tests"] * FLOP_PER["box_tests"] + cnt["tri_tests"] * FLOP_PER["tri_tests"]
@@ -282,8 +305,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
-                "config": {"workload": "cfg2: 30-icosphere scene (~24k tris, Lambert/GGX/mirror/dielectric, 1 area "
-                                       "light), 1920x1080 SLM 6.4 um, RGB 638/520/450 nm, 64 spp, depth 4, K=8",
+                "config": {"workload": wl_desc,
                            "path_samples_per_step": samples_per_step, "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MiB write)"},
                 "holograms_per_s": holo_per_s, "plain_fp64": plain, "launch_ms": launch_ms,

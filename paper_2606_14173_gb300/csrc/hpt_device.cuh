@@ -170,7 +170,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
             float3 e1 = xyz(E1), e2 = xyz(E2);
             float3 pv = cross3(d, e2);
             float det = dot3(e1, pv);
-            float idet = __frcp_rn(det);
+            float idet = __fdividef(1.0f, det);
             float3 tv = o - xyz(A);
             float u = dot3(tv, pv) * idet;
             float3 qv = cross3(tv, e1);

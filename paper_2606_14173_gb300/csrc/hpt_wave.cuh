@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
     if (p >= wd.n_paths) return;
     const PathId id = path_id(jt, wd, p);
     pb.amp[p] = 0.0f;
+    // the first coherent queue is the identity; paths of pixels outside a ragged SLM are marked
+    if (p == 0) scr->qcount[0][0] = wd.n_paths;
+    pb.q[0][0][p] = id.valid ? p : (p | Q_FINALIZE);
     if (!id.valid) return;
     const DevJob &J = *id.J;
     const float4 u = path_draw(J, id.pix, (unsigned)id.s, 0u, 0u, (unsigned)id.lam);
@@ -150,7 +153,6 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
     const float3 of = tof3(co), df_ = tof3(cd);
     pb.ray_o[p] = make_float4(of.x, of.y, of.z, 1e30f);
     pb.ray_d[p] = make_float4(df_.x, df_.y, df_.z, __int_as_float(-1));
-    enqueue(pb.q[0][0], &scr->qcount[0][0], p);
 }
 
 // ------------------------------------------------------------------------------------ s3
@@ -183,8 +185,13 @@ __device__ __forceinline__ bool exact_hit(const DevScene &sc, int tri, const R3<
     return r_nonneg<R>(b1) && r_nonneg<R>(b2) && r_nonneg<R>(RO::f(1.0f) - b1 - b2);
 }
 
+// resident blocks per SM the trace kernel is compiled for (bounds its registers)
+#ifndef HPT_TRACE_MINB
+#define HPT_TRACE_MINB 8
+#endif
+
 template <class R, bool STATS>
-__global__ void __launch_bounds__(TRACE_BLOCK) k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
+__global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
                                                        SlotScratch *__restrict__ scr, int it)
 {
     using RO = RealOps<R>;
@@ -201,7 +208,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) k_trace(const JobTable *__restric
         else if (idx < nc + ni) { kind = 1; qi = idx - nc; }
         else { kind = 2; qi = idx - nc - ni; }
         const int e = pb.q[kind][par][qi];
-        if (kind == 1 && (e & Q_FINALIZE)) continue;   // a path that only waits for its shadow ray
+        if (kind < 2 && (e & Q_FINALIZE)) continue;   // no ray: a path that only waits for its shadow ray, or none
         const int p = e;
         const DevScene &sc = jt->jobs[wd.seg[seg_of_path(wd, p)].job].sc;
         const float4 o4 = pb.ray_o[p], d4 = pb.ray_d[p];
@@ -426,20 +433,21 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
     return false;
 }
 
-template <class R, bool STATS>
+// COH = true: the coherent entries of the iteration; false: the incoherent ones (two kernels,
+// so that each carries only its half of the shading code)
+template <class R, bool STATS, bool COH>
 __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
                                                        SlotScratch *__restrict__ scr, int it)
 {
     using RO = RealOps<R>;
-    const int nc = scr->qcount[it][0], ni = scr->qcount[it][1];
-    const int total = nc + ni;
+    const int total = scr->qcount[it][COH ? 0 : 1];
     const int par = it & 1, nx = par ^ 1;
     int *const qn[3] = {pb.q[0][nx], pb.q[1][nx], pb.q[2][nx]};
     int *qcn = scr->qcount[it + 1];
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int idx = blockIdx.x * SHADE_BLOCK + threadIdx.x; idx < total; idx += gridDim.x * SHADE_BLOCK) {
-        const bool coh = idx < nc;
-        const int e = coh ? pb.q[0][par][idx] : pb.q[1][par][idx - nc];
+        const int e = pb.q[COH ? 0 : 1][par][idx];
+        if (COH && (e & Q_FINALIZE)) continue;
         const int p = e & 0x7FFFFFFF;
         const PathId id = path_id(jt, wd, p);
         const DevJob &J = *id.J;
@@ -448,7 +456,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
         Surf S;
         float3 wo = f3(0.0f, 0.0f, 1.0f);
         bool do_vertex = false;
-        if (coh) {
+        if constexpr (COH) {
             const int tri = __float_as_int(pb.hit[p].w);
             if (tri >= 0) {
                 R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));

@@ -21,8 +21,13 @@ template <class R> struct WaveLaunch {
     static cudaError_t shade(bool stats, const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr,
                              int it, int grid, cudaStream_t s)
     {
-        if (stats) k_shade<R, true><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
-        else k_shade<R, false><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        if (stats) {
+            k_shade<R, true, true><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+            k_shade<R, true, false><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        } else {
+            k_shade<R, false, true><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+            k_shade<R, false, false><<<grid, SHADE_BLOCK, 0, s>>>(jt, wd, pb, scr, it);
+        }
         return cudaGetLastError();
     }
     static cudaError_t accum(const JobTable *jt, const WaveDesc &wd, const PathBufs &pb, SlotScratch *scr, cudaStream_t s)
@@ -37,7 +42,7 @@ template <class R> struct WaveLaunch {
         int nb = 0;
         cudaError_t e = which == 0
                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace<R, false>, TRACE_BLOCK, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<R, false>, SHADE_BLOCK, 0);
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<R, false, true>, SHADE_BLOCK, 0);
         return (e == cudaSuccess && nb > 0) ? nb : 1;
     }
 };
