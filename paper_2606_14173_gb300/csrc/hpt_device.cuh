@@ -393,13 +393,12 @@ __device__ __forceinline__ float schlick(float F0, float c)
     return F0 + (1.0f - F0) * m2 * m2 * m;
 }
 
-// BSDF value and sampling pdf of a non-delta material (world-frame directions)
-__device__ __forceinline__ void bsdf_eval(const DevScene &sc, const MatDev &M, const Surf &S, float3 ns, float3 wo,
-                                          float3 wi, int ch, float &f, float &pdf)
+// BSDF value and sampling pdf of a non-delta material (world-frame directions); a = albedo
+__device__ __forceinline__ void bsdf_eval(const MatDev &M, float a, float3 ns, float3 wo, float3 wi, float &f,
+                                          float &pdf)
 {
     f = 0.0f;
     pdf = 0.0f;
-    float a = albedo_of(sc, M, S, ch);
     if (M.kind == 0) {
         float c = dot3(wi, ns);
         if (c <= 0.0f) return;

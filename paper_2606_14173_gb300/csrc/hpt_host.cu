@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -102,7 +103,8 @@ struct Builder {
     std::vector<int> idx;
     std::vector<BuildNode> nodes;
     int max_depth_seen = 0;
-    static constexpr int BINS = 32, LEAF_MAX = 4, DEPTH_LIMIT = 56;
+    // depth <= TSTACK - 1: a near-first traversal then never holds more than TSTACK entries
+    static constexpr int BINS = 32, LEAF_MAX = 4, DEPTH_LIMIT = TSTACK - 1;
 
     Builder(const std::vector<Box> &pb_, const std::vector<float> &c_, std::vector<int> prims)
         : pb(pb_), cent(c_), idx(std::move(prims)) {}
@@ -434,7 +436,6 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     std::vector<float4> knodes;
     std::vector<int> order;   // triangle ids in leaf order
     order.reserve(B.idx.size());
-    std::vector<std::pair<int, int>> todo;   // (build node, kernel node slot)
     auto emit_leaf_link = [&](const BuildNode &n) {
         int start = (int)order.size();
         for (int i = n.start; i < n.start + n.count; ++i) order.push_back(B.idx[i]);
@@ -451,33 +452,19 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
             }
         }
     };
-    // root: an inner node whose children are the build root's children (or the root leaf)
-    std::vector<const BuildNode *> kchild;   // per kernel node: two children
-    std::vector<int> stack_build;
-    {
-        const BuildNode &r = B.nodes[root];
-        const BuildNode *c0 = r.count ? &r : &B.nodes[r.left];
-        const BuildNode *c1 = r.count ? nullptr : &B.nodes[r.right];
-        kchild.push_back(c0);
-        kchild.push_back(c1);
-        knodes.resize(4);
-    }
-    for (size_t kn = 0; kn < kchild.size() / 2; ++kn) {
-        const BuildNode *c[2] = {kchild[2 * kn], kchild[2 * kn + 1]};
+    // kernel nodes in depth-first order (a node's first child follows it in memory): the root
+    // is an inner node whose children are the build root's children (or the root leaf)
+    std::function<int(const BuildNode *, const BuildNode *)> emit = [&](const BuildNode *c0, const BuildNode *c1) -> int {
+        const int kn = (int)(knodes.size() / 4);
+        knodes.resize(knodes.size() + 4);
+        const BuildNode *c[2] = {c0, c1};
         float lo[2][3], hi[2][3];
         int link[2];
-        for (int s = 0; s < 2; ++s) {
-            box_of(c[s], lo[s], hi[s]);
-            if (!c[s]) {
-                link[s] = ~0;   // empty leaf, never entered
-            } else if (c[s]->count) {
-                link[s] = emit_leaf_link(*c[s]);
-            } else {
-                link[s] = (int)(kchild.size() / 2);
-                kchild.push_back(&B.nodes[c[s]->left]);
-                kchild.push_back(&B.nodes[c[s]->right]);
-                knodes.resize(knodes.size() + 4);
-            }
+        for (int s2 = 0; s2 < 2; ++s2) {
+            box_of(c[s2], lo[s2], hi[s2]);
+            if (!c[s2]) link[s2] = ~0;   // empty leaf, never entered
+            else if (c[s2]->count) link[s2] = emit_leaf_link(*c[s2]);
+            else link[s2] = emit(&B.nodes[c[s2]->left], &B.nodes[c[s2]->right]);
         }
         float4 *o = &knodes[4 * kn];
         o[0] = make_float4(lo[0][0], hi[0][0], lo[0][1], hi[0][1]);
@@ -487,6 +474,12 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
         memcpy(&l0, &link[0], 4);
         memcpy(&l1, &link[1], 4);
         o[3] = make_float4(l0, l1, 0.0f, 0.0f);
+        return kn;
+    };
+    {
+        const BuildNode &r = B.nodes[root];
+        if (r.count) emit(&r, nullptr);
+        else emit(&B.nodes[r.left], &B.nodes[r.right]);
     }
     const int n_knodes = (int)(knodes.size() / 4);
     const int n_order = (int)order.size();

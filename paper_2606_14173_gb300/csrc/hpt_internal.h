@@ -6,7 +6,10 @@
 namespace hpt {
 
 constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
-constexpr int TSTACK = 48;         // traversal stack entries per thread (shared memory)
+#ifndef HPT_TSTACK
+#define HPT_TSTACK 32
+#endif
+constexpr int TSTACK = HPT_TSTACK; // traversal stack entries per thread (shared memory)
 constexpr int TRACE_BLOCK = 128;   // threads per block of the trace kernel
 constexpr int SHADE_BLOCK = 128;
 constexpr int GEN_BLOCK = 256;

@@ -345,6 +345,7 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
         return true;
     }
     const float3 org = S.p + ng * INC_OFFSET;
+    const float alb = albedo_of(sc, M, S, ch);
     bool shadow = false;
     st.nee = 0.0f;
     if (sc.n_lights > 0) {
@@ -363,7 +364,7 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
         const float Ll = Lt.Le[ch];
         if (cl > 0.0f && dot3(wl, ng) > 0.0f && dot3(wl, ns) > 0.0f && Ll > 0.0f) {
             float f, pbs;
-            bsdf_eval(sc, M, S, ns, wo, wl, ch, f, pbs);
+            bsdf_eval(M, alb, ns, wo, wl, f, pbs);
             const float pl = dist * dist / (cl * Lt.area) / (float)sc.n_lights;
             if (f > 0.0f) {
                 const float wm = v < J.max_depth ? pl * pl / (pl * pl + pbs * pbs) : 1.0f;
@@ -386,7 +387,7 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
             const float z = sqrtf(1.0f - u.z);
             wi = t * (rr * c_) + b * (rr * s_) + ns * z;
             bounce = dot3(wi, ng) > 0.0f;
-            weight = albedo_of(sc, M, S, ch);
+            weight = alb;
             pbs = z * INV_PI_F;
         } else {
             const float al = M.rough * M.rough;
@@ -409,8 +410,7 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
                 const float c = dot3(lo, ne);
                 const float3 li = ne * (2.0f * c) - lo;
                 if (li.z > 0.0f) {
-                    const float a = albedo_of(sc, M, S, ch);
-                    weight = schlick(a, dot3(li, ne)) * ggx_G1(al, li);
+                    weight = schlick(alb, dot3(li, ne)) * ggx_G1(al, li);
                     pbs = ggx_G1(al, lo) * ggx_D(al, ne) / (4.0f * lo.z);
                     wi = t * li.x + b * li.y + ns * li.z;
                     bounce = dot3(wi, ng) > 0.0f;

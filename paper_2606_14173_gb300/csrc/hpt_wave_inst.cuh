@@ -1,5 +1,7 @@
 // Host-side launchers of the wavefront kernels for one coherent arithmetic R.
 #pragma once
+#include <algorithm>
+
 #include "hpt_wave.cuh"
 
 namespace hpt {
@@ -36,9 +38,20 @@ template <class R> struct WaveLaunch {
         if (g > 0) k_accum<R><<<g, ACCUM_BLOCK, 0, s>>>(jt, wd, pb, scr);
         return cudaGetLastError();
     }
-    // resident blocks per SM of the trace (0) and shade (1) kernels
+    // resident blocks per SM of the trace (0) and shade (1) kernels; the trace kernel asks for
+    // no more shared memory than its traversal stacks need, leaving the rest of the SM's on-chip
+    // memory to the L1 cache that holds the BVH
     static int occupancy(int which)
     {
+        if (which == 0) {
+            int dev = 0, smem_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            const int need = HPT_TRACE_MINB * (TSTACK * TRACE_BLOCK * 4 + 1024);
+            const int pct = smem_sm > 0 ? std::min(100, (need * 100 + smem_sm - 1) / smem_sm) : 100;
+            cudaFuncSetAttribute(k_trace<R, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_trace<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        }
         int nb = 0;
         cudaError_t e = which == 0
                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace<R, false>, TRACE_BLOCK, 0)
