@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-counters", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--workload", default="cfg2", choices=list(WORKLOADS),
                    help="cfg2 = the headline workload; the others are smaller cases of the same kernels for profiling")
     return p.parse_args()
@@ -150,6 +151,73 @@ def cpu_oracle_rate(scene, r, n_pixels, seed=5):
     dt = time.perf_counter() - t0
     samples = n_pixels * len(r.lambdas) * r.spp
     return samples / dt, dt, cores, samples
+
+
+def _pose_T(dx, dy, dz):
+    """Rigid world -> hologram transform of an eye offset (dx, dy) and an axial focus shift dz."""
+    T = np.eye(4)
+    T[0, 3], T[1, 3], T[2, 3] = -dx, -dy, -dz
+    return T
+
+
+def serve(ctx, hpt, S, requests, rate, seed):
+    """Submit requests with Poisson arrivals at 'rate' per second; returns latency statistics.
+    requests: list of (scene id, render, precision, output tensor)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(requests))
+    torch.cuda.synchronize()
+    ids, t0 = [], time.perf_counter()
+    t_next = t0
+    for (sid, r, prec, out), g in zip(requests, gaps):
+        t_next += g
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(ctx.submit(sid, r, out, precision=prec))
+    for i in ids:
+        ctx.wait(i, 600000)
+    times = np.array([ctx.request_times(i) for i in ids]) / 1e6
+    lat = times[:, 2] - times[:, 0]
+    span = times[:, 2].max() - times[:, 0].min()
+    holos = sum(r.K for _, r, _, _ in requests)
+    return {"requests": len(ids), "offered_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s": float(np.mean(times[:, 1] - times[:, 0])),
+            "holograms_per_s": holos / span, "path_samples_per_s": sum(r.path_samples() for _, r, _, _ in requests) / span,
+            "span_s": float(span)}
+
+
+def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
+    """(a) headline requests (1080p RGB 64 spp depth 4 K=8) at 2 req/s, near the device's capacity;
+    (b) a mixed request stream at 40 req/s following the serving recipe (poses, focal depths,
+    SLM sizes, spp, K, scenes), scaled to 512x512 and 1920x1080 SLMs and spp <= 64 so that it ends
+    in seconds."""
+    rng = np.random.default_rng(4242)
+    head = [(sid_cfg1, S.config2_render(seed=10 + k), hpt.PREC_DF32, None) for k in range(6)]
+    head = [(sid, r, prec, hpt.alloc_output(r)) for sid, r, prec, _ in head]
+    a = serve(ctx, hpt, S, head, 2.0, 7)
+    a["workload"] = "6 requests of the headline render (1920x1080 RGB, 64 spp, depth 4, K=8), Poisson 2 req/s"
+    del head
+    mix = []
+    z_med = {sid_cfg0: 7.5e-3, sid_cfg1: 17.5e-3}
+    for k in range(24):
+        sid = sid_cfg1 if rng.random() < 0.6 else sid_cfg0
+        big = rng.random() < 0.4
+        W, H = (1920, 1080) if big else (512, 512)
+        spp = int(rng.choice([16, 32, 64]))
+        K = int(rng.choice([1, 4, 8]))
+        dx, dy = rng.uniform(-5e-3, 5e-3, 2)
+        df = rng.uniform(5e-3, 30e-3)
+        if sid == sid_cfg1:
+            r = S.config1_render(W=W, H=H, spp=spp, K=K, seed=100 + k, T=_pose_T(dx, dy, z_med[sid] - df))
+        else:
+            r = S.config0_render(W=W, H=H, spp=spp, K=K, seed=100 + k, pitch=6.4e-6,
+                                 T=_pose_T(dx * 0.1, dy * 0.1, 0.0))
+        mix.append((sid, r, hpt.PREC_DF32, hpt.alloc_output(r)))
+    b = serve(ctx, hpt, S, mix, 40.0, 8)
+    b["workload"] = ("24 requests, Poisson 40 req/s: scenes cfg1 (60%) / cfg0, SLM 512x512 or 1920x1080, spp in "
+                     "{16,32,64}, K in {1,4,8}, eye offsets U[-5,5] mm, focal depth U[5,30] mm")
+    return {"headline_requests": a, "mixed_stream": b}
 
 
 def run_reference(args):
@@ -294,6 +362,12 @@ def main():
                 "per_sample": {k: v / ns for k, v in cnt.items() if k != "samples"},
                 "flops_per_sample": flops / ns}
 
+    serving = None
+    if not args.no_serving and args.workload == "cfg2":
+        sid0 = ctx.upload_scene(S.config0_scene())
+        serving = run_serving(ctx, hpt, S, sid, sid0)
+        ctx.sync()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, cores, nsamp = cpu_oracle_rate(sc, r, 8192)
@@ -309,7 +383,7 @@ def main():
                            "path_samples_per_step": samples_per_step, "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MiB write)"},
                 "holograms_per_s": holo_per_s, "plain_fp64": plain, "launch_ms": launch_ms,
-                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -214,17 +214,19 @@ struct Slot {
 };
 
 struct Request {
-    uint64_t id;
-    uint64_t scene;
-    DevJob job;         // with out pointer
-    int prec;
-    long long n_items;  // items of the whole request
-    long long next = 0; // next item to schedule
-    int steps_in_flight = 0;
-    size_t out_bytes;
+    uint64_t id = 0;
+    SceneRec *scene = nullptr;
+    DevJob job{};
+    int prec = 1;
+    long long next = 0;          // next work item to schedule
+    size_t out_bytes = 0;
     double t_submit = 0, t_admit = -1, t_done = -1;
     bool done = false;
-    hpt_status err = HPT_OK;
+};
+
+struct InflightWave {
+    cudaEvent_t ev = nullptr;
+    std::vector<std::shared_ptr<Request>> finishing;   // requests whose last items are in this wave
 };
 
 struct hpt_ctx {
@@ -250,15 +252,20 @@ struct hpt_ctx {
     size_t host_out_bytes = 0;
     std::chrono::steady_clock::time_point t0;
     // serving
-    uint64_t budget = 0;
-    int max_inflight = 8;
+    uint64_t budget = 0;                 // device bytes of in-flight request outputs
+    int max_inflight = 8;                // requests on the device at once
+    size_t max_queue = 4096;             // pending requests before hpt_submit says BUSY
     std::mutex smu;
     std::condition_variable scv, dcv;
     std::deque<std::shared_ptr<Request>> pending;
     std::vector<std::shared_ptr<Request>> active;
     std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    std::deque<InflightWave> inflight;
+    std::vector<cudaEvent_t> free_events;
     uint64_t next_req = 1;
-    uint64_t bytes_active = 0;
+    uint64_t bytes_active = 0;           // outputs of admitted, not yet finished requests
+    int live = 0;                        // admitted, not yet finished requests
+    size_t rr = 0;
     bool stop = false;
     std::thread sched;
     cudaStream_t sstream = nullptr;
@@ -347,6 +354,8 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->sched.joinable()) ctx->sched.join();
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (auto &w : ctx->inflight) cudaEventDestroy(w.ev);
+    for (auto e : ctx->free_events) cudaEventDestroy(e);
     for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
     for (auto &s : ctx->slots) {
         cudaFree(s.d_table);
@@ -967,17 +976,241 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
 }
 
 // ------------------------------------------------------------------------------ serving
-static void sched_loop(hpt_ctx *ctx) { (void)ctx; }
-
-extern "C" hpt_status hpt_submit(hpt_ctx *, uint64_t, const hpt_render_desc *, void *, size_t, uint64_t *)
+// Continuous batching.  A scheduler thread admits queued requests while fewer than
+// max_inflight are active and their outputs fit the HBM budget, then keeps the device busy
+// with waves: each wave takes an equal share of its paths from every active request of one
+// arithmetic (round robin), so requests that arrive while others are running join the next
+// wave and their work overlaps on the device.  Two waves are queued ahead; a request is
+// complete when the wave that carries its last items finishes.  Per-pixel results do not
+// depend on how items are grouped into waves, so a request's fields are the same alone and in
+// the mix.
+static void retire_oldest(hpt_ctx *ctx)
 {
-    return fail(HPT_ERR_UNSUPPORTED, "serving not built yet");
+    InflightWave w;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        if (ctx->inflight.empty()) return;
+        w = ctx->inflight.front();
+    }
+    cudaEventSynchronize(w.ev);
+    const double now = ctx->now_us();
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->inflight.pop_front();
+        ctx->free_events.push_back(w.ev);
+        for (auto &r : w.finishing) {
+            r->done = true;
+            r->t_done = now;
+            ctx->bytes_active -= r->out_bytes;
+            ctx->live--;
+            r->scene->users--;
+        }
+    }
+    ctx->dcv.notify_all();
+    ctx->scv.notify_all();
 }
-extern "C" hpt_status hpt_poll(hpt_ctx *, uint64_t, int *) { return fail(HPT_ERR_UNSUPPORTED, "serving not built yet"); }
-extern "C" hpt_status hpt_wait(hpt_ctx *, uint64_t, uint32_t) { return fail(HPT_ERR_UNSUPPORTED, "serving not built yet"); }
-extern "C" hpt_status hpt_request_times(hpt_ctx *, uint64_t, double *)
+
+static void sched_loop(hpt_ctx *ctx)
 {
-    return fail(HPT_ERR_UNSUPPORTED, "serving not built yet");
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        std::vector<std::pair<std::shared_ptr<Request>, int>> picks;
+        int prec = -1;
+        bool idle_wait = false;
+        {
+            std::unique_lock<std::mutex> lk(ctx->smu);
+            auto schedulable = [&] {
+                for (auto &r : ctx->active)
+                    if (r->next < r->job.n_items) return true;
+                return false;
+            };
+            ctx->scv.wait(lk, [&] {
+                return ctx->stop || !ctx->pending.empty() || schedulable() || !ctx->inflight.empty();
+            });
+            if (ctx->stop && ctx->inflight.empty()) break;
+            if (ctx->stop) {
+                idle_wait = true;   // drain what is in flight, start nothing new
+                goto unlocked;
+            }
+            // admission: slots and HBM budget
+            while (!ctx->stop && !ctx->pending.empty() && ctx->live < ctx->max_inflight &&
+                   (ctx->live == 0 || ctx->bytes_active + ctx->pending.front()->out_bytes <= ctx->budget)) {
+                auto r = ctx->pending.front();
+                ctx->pending.pop_front();
+                r->t_admit = ctx->now_us();
+                ctx->bytes_active += r->out_bytes;
+                ctx->live++;
+                ctx->active.push_back(r);
+            }
+            // one wave: equal path shares of the active requests that use one arithmetic
+            std::vector<std::shared_ptr<Request>> cand;
+            const size_t na = ctx->active.size();
+            for (size_t k = 0; k < na; ++k) {
+                auto &r = ctx->active[(ctx->rr + k) % na];
+                if (r->next >= r->job.n_items) continue;
+                if (prec < 0) prec = r->prec;
+                if (r->prec == prec && (int)cand.size() < MAX_SEG) cand.push_back(r);
+            }
+            if (!cand.empty()) {
+                ctx->rr = (ctx->rr + 1) % std::max<size_t>(na, 1);
+                const long long share = std::max<long long>(1, (long long)ctx->capacity / (long long)cand.size());
+                for (auto &r : cand) {
+                    long long take = std::max<long long>(1, share / r->job.spp);
+                    take = std::min<long long>(take, r->job.n_items - r->next);
+                    picks.push_back({r, (int)take});
+                }
+            } else {
+                idle_wait = !ctx->inflight.empty();
+            }
+        }
+    unlocked:
+        if (!picks.empty()) {
+            hpt_status st = HPT_OK;
+            InflightWave w;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                st = ensure_paths(ctx);
+                Slot *slot = st ? nullptr : acquire_slot(ctx);
+                WaveDesc wd;
+                memset(&wd, 0, sizeof wd);
+                int max_depth = 1;
+                if (slot) {
+                    JobTable *h = slot->h_table;
+                    h->n_jobs = 0;
+                    for (auto &pk : picks) {
+                        Request &r = *pk.first;
+                        const int j = h->n_jobs++;
+                        h->jobs[j] = r.job;
+                        WaveSeg &g = wd.seg[wd.n_seg++];
+                        g.job = j;
+                        g.spp = r.job.spp;
+                        g.item_begin = r.next;
+                        g.item_count = pk.second;
+                        g.path_offset = wd.n_paths;
+                        wd.n_paths += pk.second * r.job.spp;
+                        wd.n_items += pk.second;
+                        max_depth = std::max(max_depth, r.job.max_depth);
+                    }
+                    cudaStream_t ws = ctx->wstream;
+                    const int n_iter = max_depth + 1;
+                    bool ok = cudaMemcpyAsync(slot->d_table, h, offsetof(JobTable, jobs) + sizeof(DevJob) * h->n_jobs,
+                                              cudaMemcpyHostToDevice, ws) == cudaSuccess;
+                    ok = ok && cudaMemsetAsync(ctx->d_scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws) == cudaSuccess;
+                    ok = ok && wave_gen(prec, slot->d_table, wd, ctx->pb, ctx->d_scr, ws) == cudaSuccess;
+                    for (int it = 0; ok && it < n_iter; ++it) {
+                        ok = wave_trace(prec, false, slot->d_table, wd, ctx->pb, ctx->d_scr, it, ctx->grid_trace[prec], ws) == cudaSuccess;
+                        ok = ok && wave_shade(prec, false, slot->d_table, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws) == cudaSuccess;
+                    }
+                    ok = ok && wave_accum(prec, slot->d_table, wd, ctx->pb, ctx->d_scr, ws) == cudaSuccess;
+                    ok = ok && cudaEventRecord(slot->done, ws) == cudaSuccess;
+                    {
+                        std::lock_guard<std::mutex> lk2(ctx->smu);
+                        if (!ctx->free_events.empty()) {
+                            w.ev = ctx->free_events.back();
+                            ctx->free_events.pop_back();
+                        }
+                    }
+                    if (!w.ev) cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
+                    ok = ok && cudaEventRecord(w.ev, ws) == cudaSuccess;
+                    if (!ok) st = HPT_ERR_CUDA;
+                }
+            }
+            {
+                std::lock_guard<std::mutex> lk(ctx->smu);
+                for (auto &pk : picks) {
+                    Request &r = *pk.first;
+                    r.next += pk.second;
+                    if (r.next >= r.job.n_items) {
+                        w.finishing.push_back(pk.first);
+                        ctx->active.erase(std::find(ctx->active.begin(), ctx->active.end(), pk.first));
+                    }
+                }
+                ctx->inflight.push_back(w);
+            }
+            (void)st;
+        }
+        // keep at most two waves queued ahead; retire finished ones
+        size_t nin;
+        {
+            std::lock_guard<std::mutex> lk(ctx->smu);
+            nin = ctx->inflight.size();
+        }
+        if (nin > 2 || (picks.empty() && (idle_wait || nin > 0))) retire_oldest(ctx);
+    }
+    // shutting down: nothing left in flight; pending requests are dropped
+}
+
+extern "C" hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_dev,
+                                 size_t out_bytes, uint64_t *req_id)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_dev || !req_id) return fail(HPT_ERR_INVALID_ARG, "out_dev or req_id is NULL");
+    auto r = std::make_shared<Request>();
+    SceneRec *rec = nullptr;
+    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, r->job, &rec);
+    if (st) return st;
+    if (r->job.spp > ctx->capacity) return fail(HPT_ERR_UNSUPPORTED, "spp exceeds the wave capacity");
+    r->scene = rec;
+    r->prec = desc->precision;
+    r->out_bytes = (size_t)8 * desc->n_lambda * desc->K * (size_t)desc->W * desc->H;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        if (ctx->stop) return fail(HPT_ERR_BUSY, "context is shutting down");
+        if (ctx->pending.size() >= ctx->max_queue) return fail(HPT_ERR_BUSY, "request queue full (%zu)", ctx->max_queue);
+        r->id = ctx->next_req++;
+        r->t_submit = ctx->now_us();
+        rec->users++;
+        ctx->pending.push_back(r);
+        ctx->reqs[r->id] = r;
+        *req_id = r->id;
+    }
+    ctx->scv.notify_all();
+    return HPT_OK;
+}
+
+static std::shared_ptr<Request> find_req(hpt_ctx *ctx, uint64_t id)
+{
+    auto it = ctx->reqs.find(id);
+    return it == ctx->reqs.end() ? nullptr : it->second;
+}
+
+extern "C" hpt_status hpt_poll(hpt_ctx *ctx, uint64_t req_id, int *done)
+{
+    g_err.clear();
+    if (!ctx || !done) return fail(HPT_ERR_INVALID_ARG, "ctx or done is NULL");
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto r = find_req(ctx, req_id);
+    if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+    *done = r->done ? 1 : 0;
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_ms)
+{
+    g_err.clear();
+    if (!ctx) return fail(HPT_ERR_INVALID_ARG, "ctx is NULL");
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    auto r = find_req(ctx, req_id);
+    if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+    if (timeout_ms == 0) ctx->dcv.wait(lk, [&] { return r->done; });
+    else if (!ctx->dcv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
+        return fail(HPT_ERR_TIMEOUT, "request %llu not done after %u ms", (unsigned long long)req_id, timeout_ms);
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[3])
+{
+    g_err.clear();
+    if (!ctx || !t) return fail(HPT_ERR_INVALID_ARG, "ctx or t is NULL");
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto r = find_req(ctx, req_id);
+    if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+    t[0] = r->t_submit;
+    t[1] = r->t_admit;
+    t[2] = r->t_done;
+    return r->done ? HPT_OK : fail(HPT_ERR_BUSY, "request %llu not done", (unsigned long long)req_id);
 }
 
 // ------------------------------------------------------------ accessors for hpt_static.cu
