@@ -62,10 +62,14 @@ enum { HPT_PREC_FP64 = 0, HPT_PREC_DF32 = 1 };
 
 typedef struct hpt_ctx hpt_ctx;
 
+/* context flags */
+enum { HPT_CTX_NO_GRAPHS = 1 };   /* hpt_trace launches every kernel instead of replaying frames */
+
 typedef struct {
-    uint64_t hbm_budget_bytes;  /* serving admission limit for in-flight outputs; 0 = free HBM */
-    int32_t max_inflight;       /* serving: requests on the device at once (0 -> 8)           */
-    int32_t flags;              /* reserved, 0                                                 */
+    uint64_t hbm_budget_bytes;  /* serving admission limit for in-flight outputs; 0 = 60 % of
+                                   the free HBM at creation                                   */
+    int32_t max_inflight;       /* serving: requests admitted and not finished (0 -> 8)       */
+    int32_t flags;              /* HPT_CTX_* bits                                              */
 } hpt_ctx_desc;
 
 /* Scene description.  All arrays are host memory, read during hpt_scene_upload only.
@@ -163,7 +167,11 @@ hpt_status hpt_scene_info(hpt_ctx *ctx, uint64_t scene_id, uint64_t *device_byte
 
 /* Trace one render description into the caller's device buffer, asynchronously on
  * 'cuda_stream' (a cudaStream_t, NULL = legacy default stream).  All wavelengths and all K
- * holograms are produced by one persistent kernel launch. */
+ * holograms are produced by one launch group (waves of generate / trace / shade / accumulate
+ * kernels).  The first call with a given launch shape (arithmetic, out_dev, SLM size x
+ * wavelengths, spp, max_depth) captures the frame as a CUDA graph; later calls replay it (up to
+ * 8 shapes are kept, least recently used first out).  Calls on one context are serialised on
+ * one internal stream, linked to cuda_stream by events. */
 hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                      void *out_dev, size_t out_bytes, void *cuda_stream);
 /* Same, end to end with host memory: the result is copied into out_host (pinned or pageable)
@@ -180,6 +188,14 @@ hpt_status hpt_sync(hpt_ctx *ctx);
 enum { HPT_NCOUNTERS = 8 };
 hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                               void *out_dev, size_t out_bytes, uint64_t counters[HPT_NCOUNTERS]);
+
+/* Choose the context's wave size (paths per wave: 1M .. 16M, within half of the free HBM) by
+ * timing hpt_trace of a 128-row band of 'desc' (spp capped at 32) for each candidate; keeps the
+ * fastest (a larger wave must win by more than 2 %), reallocates the wave state and drops the
+ * captured frames.  Synchronous; *paths_per_wave receives the choice.  Results of later traces
+ * do not depend on the wave size. */
+hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                        int32_t *paths_per_wave);
 
 /* ---- serving: continuous batching of render requests ---------------------------------- */
 /* Queue a request; the scheduler thread admits it when a slot and memory are free and runs

@@ -238,6 +238,20 @@ struct hpt_ctx {
     void *pb_arena = nullptr;
     int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
+    // captured frames of hpt_trace, keyed by what fixes the launch sequence
+    struct FrameGraph {
+        int prec = 0, spp = 0, max_depth = 0, capacity = 0;
+        long long n_items = 0;
+        void *out = nullptr;
+        JobTable *d_table = nullptr, *h_table = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        bool used = false;
+        uint64_t last_use = 0;
+    };
+    std::vector<FrameGraph> graphs;
+    bool use_graphs = true;
+    uint64_t graph_clock = 0;
     SlotScratch *d_scr = nullptr;
     cudaStream_t wstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -306,6 +320,8 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     }
     if (const char *e = getenv("HPT_WAVE_PATHS")) ctx->capacity = std::max(1 << 12, std::min(atoi(e), 1 << 26));
     if (const char *e = getenv("HPT_DEBUG_WAVES")) ctx->debug_waves = atoi(e);
+    if (desc && (desc->flags & HPT_CTX_NO_GRAPHS)) ctx->use_graphs = false;
+    if (const char *e = getenv("HPT_GRAPHS")) ctx->use_graphs = atoi(e) != 0;
     CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
     CUDA_TRY(cudaMemset(ctx->d_scr, 0, sizeof(SlotScratch)));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
@@ -355,6 +371,12 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto &w : ctx->inflight) cudaEventDestroy(w.ev);
+    for (auto &g : ctx->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaEventDestroy(g.done);
+        cudaFree(g.d_table);
+        cudaFreeHost(g.h_table);
+    }
     for (auto e : ctx->free_events) cudaEventDestroy(e);
     for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
     for (auto &s : ctx->slots) {
@@ -813,25 +835,15 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
 
 // One launch group: the waves covering all items of 'jobs', queued on the context's wave
 // stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
-static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t user)
+// Queue the waves that cover all items of 'jobs' (job table already on the device) on ws.
+static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, const JobTable *jt,
+                                cudaStream_t ws, bool allow_debug)
 {
-    hpt_status st = ensure_paths(ctx);
-    if (st) return st;
-    Slot *slot = acquire_slot(ctx);
-    JobTable *h = slot->h_table;
-    h->n_jobs = n;
-    for (int i = 0; i < n; ++i) h->jobs[i] = jobs[i];
-    cudaStream_t ws = ctx->wstream;
-    CUDA_TRY(cudaEventRecord(ctx->ev_in, user));
-    CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
-    const size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
-    CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, ws));
-    if (stats) CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
-    const JobTable *jt = slot->d_table;
     const int B = ctx->capacity;
     WaveDesc wd;
     memset(&wd, 0, sizeof wd);
     int max_depth = 1;
+    hpt_status st = HPT_OK;
     auto flush = [&]() -> hpt_status {
         if (wd.n_seg == 0) return HPT_OK;
         const int n_iter = max_depth + 1;
@@ -842,7 +854,7 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
             CUDA_TRY(wave_shade(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws));
         }
         CUDA_TRY(wave_accum(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
-        if (ctx->debug_waves > 0) {
+        if (allow_debug && ctx->debug_waves > 0) {
             // diagnostic: queue lengths per iteration of the first waves (HPT_DEBUG_WAVES=n)
             --ctx->debug_waves;
             int q[MAX_ITER + 1][3];
@@ -880,9 +892,106 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
             c += take;
         }
     }
-    st = flush();
+    return flush();
+}
+
+// One launch group: the waves covering all items of 'jobs', queued on the context's wave
+// stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
+static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t user)
+{
+    hpt_status st = ensure_paths(ctx);
+    if (st) return st;
+    Slot *slot = acquire_slot(ctx);
+    JobTable *h = slot->h_table;
+    h->n_jobs = n;
+    for (int i = 0; i < n; ++i) h->jobs[i] = jobs[i];
+    cudaStream_t ws = ctx->wstream;
+    CUDA_TRY(cudaEventRecord(ctx->ev_in, user));
+    CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
+    const size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
+    CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, ws));
+    if (stats) CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
+    st = enqueue_waves(ctx, jobs, n, prec, stats, slot->d_table, ws, true);
     if (st) return st;
     CUDA_TRY(cudaEventRecord(slot->done, ws));
+    CUDA_TRY(cudaEventRecord(ctx->ev_out, ws));
+    CUDA_TRY(cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    return HPT_OK;
+}
+
+// A frame of one job as a captured CUDA graph: the first call with a given launch shape
+// (arithmetic, output buffer, items, spp, depth, wave capacity) captures the job-table upload
+// and every wave launch; later calls refresh the pinned job table and replay.  Caller holds
+// ctx->mu.
+static hpt_status run_graph(hpt_ctx *ctx, const DevJob &J, int prec, cudaStream_t user)
+{
+    hpt_status st = ensure_paths(ctx);
+    if (st) return st;
+    hpt_ctx::FrameGraph *g = nullptr;
+    for (auto &x : ctx->graphs)
+        if (x.prec == prec && x.out == (void *)J.out && x.n_items == J.n_items && x.spp == J.spp &&
+            x.max_depth == J.max_depth && x.capacity == ctx->capacity)
+            g = &x;
+    cudaStream_t ws = ctx->wstream;
+    const size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob);
+    if (!g) {
+        if (ctx->graphs.size() >= 8) {   // evict the least recently used frame
+            auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                        [](const hpt_ctx::FrameGraph &a, const hpt_ctx::FrameGraph &b) {
+                                            return a.last_use < b.last_use;
+                                        });
+            cudaEventSynchronize(lru->done);
+            cudaGraphExecDestroy(lru->exec);
+            cudaEventDestroy(lru->done);
+            cudaFree(lru->d_table);
+            cudaFreeHost(lru->h_table);
+            ctx->graphs.erase(lru);
+        }
+        hpt_ctx::FrameGraph x;
+        x.prec = prec;
+        x.out = (void *)J.out;
+        x.n_items = J.n_items;
+        x.spp = J.spp;
+        x.max_depth = J.max_depth;
+        x.capacity = ctx->capacity;
+        CUDA_TRY(cudaMalloc(&x.d_table, sizeof(JobTable)));
+        CUDA_TRY(cudaMallocHost(&x.h_table, sizeof(JobTable)));
+        CUDA_TRY(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
+        x.h_table->n_jobs = 1;
+        x.h_table->jobs[0] = J;
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemcpyAsync(x.d_table, x.h_table, bytes, cudaMemcpyHostToDevice, ws);
+        hpt_status st2 = e1 == cudaSuccess ? enqueue_waves(ctx, &J, 1, prec, false, x.d_table, ws, false) : HPT_ERR_CUDA;
+        cudaError_t e2 = cudaStreamEndCapture(ws, &graph);
+        if (e1 != cudaSuccess || st2 || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaFree(x.d_table);
+            cudaFreeHost(x.h_table);
+            cudaEventDestroy(x.done);
+            return st2 ? st2 : fail(HPT_ERR_CUDA, "frame capture failed: %s", cudaGetErrorString(e1 ? e1 : e2));
+        }
+        cudaError_t e3 = cudaGraphInstantiate(&x.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) {
+            cudaFree(x.d_table);
+            cudaFreeHost(x.h_table);
+            cudaEventDestroy(x.done);
+            return fail(HPT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+        }
+        ctx->graphs.push_back(x);
+        g = &ctx->graphs.back();
+    } else {
+        // the graph's copy reads the pinned table when it runs: wait for the previous replay
+        if (g->used) CUDA_TRY(cudaEventSynchronize(g->done));
+        g->h_table->jobs[0] = J;
+    }
+    g->used = true;
+    g->last_use = ++ctx->graph_clock;
+    CUDA_TRY(cudaEventRecord(ctx->ev_in, user));
+    CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
+    CUDA_TRY(cudaGraphLaunch(g->exec, ws));
+    CUDA_TRY(cudaEventRecord(g->done, ws));
     CUDA_TRY(cudaEventRecord(ctx->ev_out, ws));
     CUDA_TRY(cudaStreamWaitEvent(user, ctx->ev_out, 0));
     return HPT_OK;
@@ -899,6 +1008,7 @@ extern "C" hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_rende
     st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->use_graphs && ctx->debug_waves == 0) return run_graph(ctx, J, desc->precision, (cudaStream_t)stream);
     return run_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream);
 }
 
@@ -972,6 +1082,92 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
     CUDA_TRY(cudaMemcpy(c, ctx->d_scr->counters, sizeof c, cudaMemcpyDeviceToHost));
     for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k];
     counters[0] = (uint64_t)desc->n_lambda * desc->W * (uint64_t)desc->H * desc->spp;   // path samples
+    return read_status(ctx);
+}
+
+// ---------------------------------------------------------------------------- autotune
+static void drop_graphs(hpt_ctx *ctx)
+{
+    for (auto &g : ctx->graphs) {
+        cudaEventSynchronize(g.done);
+        cudaGraphExecDestroy(g.exec);
+        cudaEventDestroy(g.done);
+        cudaFree(g.d_table);
+        cudaFreeHost(g.h_table);
+    }
+    ctx->graphs.clear();
+}
+
+static hpt_status set_capacity(hpt_ctx *ctx, int cap)
+{
+    if (cap == ctx->capacity && ctx->pb_arena) return HPT_OK;
+    CUDA_TRY(cudaStreamSynchronize(ctx->wstream));
+    drop_graphs(ctx);
+    if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
+    ctx->pb_arena = nullptr;
+    ctx->capacity = cap;
+    return ensure_paths(ctx);
+}
+
+extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                                   int32_t *paths_per_wave)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!desc || !paths_per_wave) return fail(HPT_ERR_INVALID_ARG, "desc or paths_per_wave is NULL");
+    hpt_render_desc band = *desc;
+    band.H = std::min(desc->H, 128);
+    band.spp = std::min(desc->spp, 32);
+    DevJob J;
+    st = make_job(ctx, scene_id, &band, nullptr, 0, J, nullptr);
+    if (st) return st;
+    const size_t out_b = (size_t)8 * band.n_lambda * band.K * (size_t)band.W * band.H;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    void *out = nullptr;
+    CUDA_TRY(cudaMalloc(&out, out_b));
+    J.out = (float2 *)out;
+    const int old = ctx->capacity;
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    const size_t avail = fr + (ctx->pb_arena ? (size_t)ctx->capacity * path_bytes() : 0);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = old;
+    double best_rate = -1.0;
+    const int cands[] = {1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24};
+    for (int cap : cands) {
+        if ((size_t)cap * path_bytes() > avail / 2 || cap < J.spp) continue;
+        st = set_capacity(ctx, cap);
+        if (st) break;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3 && !st; ++rep) {
+            CUDA_TRY(cudaEventRecord(e0, ctx->wstream));
+            st = run_jobs(ctx, &J, 1, band.precision, false, ctx->wstream);
+            CUDA_TRY(cudaEventRecord(e1, ctx->wstream));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) best_ms = std::min(best_ms, ms);
+        }
+        if (st) break;
+        const double rate = (double)band.n_lambda * band.W * band.H * band.spp / best_ms;
+        if (rate > best_rate * 1.02) {   // prefer the smaller wave unless the larger is clearly faster
+            best_rate = rate;
+            best = cap;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (st) {
+        set_capacity(ctx, old);
+        return st;
+    }
+    st = set_capacity(ctx, best);
+    if (st) return st;
+    *paths_per_wave = best;
     return read_status(ctx);
 }
 

@@ -24,7 +24,7 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 # exported symbols, as declared in include/hpt.h
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
-           "hpt_request_times", "hpt_trace_fixed_scratch"]
+           "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune"]
 
 
 class HptError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_wait.argtypes = [vp, C.c_uint64, C.c_uint32]
     lib.hpt_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double)]
     lib.hpt_trace_fixed_scratch.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
+    lib.hpt_autotune.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), C.POINTER(C.c_int32)]
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("hpt_destroy", "hpt_last_error"):
@@ -125,10 +126,10 @@ def out_bytes(r) -> int:
 class Context:
     """One library context on one CUDA device (owns scenes and launch slots)."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, graphs: bool = True):
         self.lib = load_library()
         self.h = C.c_void_p()
-        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0)
+        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0 if graphs else 1)
         _check(self.lib.hpt_create(C.byref(self.h), int(device), C.byref(desc)))
         self.device = device
 
@@ -226,6 +227,13 @@ class Context:
         c = (C.c_uint64 * NCOUNTERS)()
         _check(self.lib.hpt_trace_counters(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, c))
         return dict(zip(COUNTER_NAMES, [int(x) for x in c]))
+
+    def autotune(self, sid: int, r, precision=PREC_DF32) -> int:
+        """Pick the wave size by timing a band of this render; returns paths per wave."""
+        d = render_desc(r, precision)
+        n = C.c_int32()
+        _check(self.lib.hpt_autotune(self.h, C.c_uint64(sid), C.byref(d), C.byref(n)))
+        return n.value
 
     def sync(self):
         _check(self.lib.hpt_sync(self.h))
