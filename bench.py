@@ -37,12 +37,14 @@ ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
 
 
-# name -> (description, render overrides of the 1080p RGB K=8 headline render)
+# name -> (description, scene factory, render factory)
 WORKLOADS = {
     "cfg2": ("cfg2: 30-icosphere scene (~24k tris, Lambert/GGX/mirror/dielectric, 1 area light), 1920x1080 SLM 6.4 um, "
-             "RGB 638/520/450 nm, 64 spp, depth 4, K=8", {}),
+             "RGB 638/520/450 nm, 64 spp, depth 4, K=8", "config1_scene", ("config2_render", {})),
     "band": ("profiling case: the cfg2 scene and SLM pitch, a 1920x270 band at mid height, RGB, 16 spp, depth 4, K=8",
-             {"H": 270, "spp": 16}),
+             "config1_scene", ("config2_render", {"H": 270, "spp": 16})),
+    "cfg3": ("cfg3: ~185k tris (icospheres + subdivided GGX/dielectric slabs), 128^3 binary16 ambient cache past the "
+             "first bounce, 3840x2160 SLM 3.74 um, RGB, 256 spp, depth 4, K=8", "config3_scene", ("config3_render", {})),
 }
 
 
@@ -227,11 +229,12 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = S.config1_scene()
-    r = S.config2_render()
-    n_pix = 2048
+    wl_desc, scene_fn, (render_fn, wl_over) = WORKLOADS[args.workload]
+    sc = getattr(S, scene_fn)()
+    r = getattr(S, render_fn)(**wl_over)
+    n_pix = 2048 if args.workload != "cfg3" else 256
     for _ in range(args.warmup):
-        cpu_oracle_rate(sc, r, 256)
+        cpu_oracle_rate(sc, r, max(n_pix // 8, 16))
     rates, dts, samples = [], [], 0
     for k in range(args.steps):
         rate, dt, cores, ns = cpu_oracle_rate(sc, r, n_pix, seed=100 + k)
@@ -239,14 +242,13 @@ def run_reference(args):
         samples += ns
     total = sum(dts)
     value = samples / total
+    sample = (f"{n_pix} seeded random pixels of the {r.W}x{r.H} frame per step, {len(r.lambdas)} wavelengths, "
+              f"{r.spp} spp, K={r.K}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cfg2: 30-icosphere scene (~24k tris), 1920x1080 SLM 6.4 um, RGB, 64 spp, "
-                                   "depth 4, K=8", "sample": f"{n_pix} random pixels x 3 wavelengths x 64 spp per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{n_pix} seeded random pixels of the 1080p frame per step, all 3 wavelengths, "
-                                       f"64 spp, K=8"},
+            "config": {"workload": wl_desc, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -264,10 +266,11 @@ def main():
         pbuild.build()
     barrier(world)
     ctx = hpt.Context(local)
-    sc = S.config1_scene()
+    wl_desc, scene_fn, (render_fn, wl_over) = WORKLOADS[args.workload]
+    sc = getattr(S, scene_fn)()
     sid = ctx.upload_scene(sc)
-    wl_desc, wl_over = WORKLOADS[args.workload]
-    r = S.config2_render(seed=1 + rank, **wl_over)
+    make_render = getattr(S, render_fn)
+    r = make_render(seed=1 + rank, **wl_over)
     samples_per_step = r.path_samples()
     out = hpt.alloc_output(r)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
@@ -279,7 +282,7 @@ def main():
     def step_mixed():
         ctx.trace(sid, r, out, precision=hpt.PREC_DF32, stream=stream)
 
-    r_plain = [S.config2_render(seed=1 + rank, lambdas=(l,), channels=(c,), **wl_over)
+    r_plain = [make_render(seed=1 + rank, lambdas=(l,), channels=(c,), **wl_over)
                for l, c in zip(r.lambdas, r.channels)]
     outs_plain = [hpt.alloc_output(rp) for rp in r_plain]
 
@@ -370,10 +373,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, cores, nsamp = cpu_oracle_rate(sc, r, 8192)
+        npx = 8192 if args.workload != "cfg3" else 1024
+        rate, dt, cores, nsamp = cpu_oracle_rate(sc, r, npx)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"8192 seeded random pixels of the 1080p frame x 3 wavelengths x 64 spp "
-                         f"({nsamp} path samples, {dt:.1f} s)"}
+               "sample": f"{npx} seeded random pixels of the {r.W}x{r.H} frame x {len(r.lambdas)} wavelengths x "
+                         f"{r.spp} spp ({nsamp} path samples, {dt:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -321,7 +321,7 @@ static int closest(const oracle_t *o, v3 org, v3 dir, double tmin, double tmax, 
 }
 
 /* any hit with tmin < t < tmax, skipping 'skip' */
-static int occluded(const oracle_t *o, v3 org, v3 dir, double tmax, int skip, int *nearf)
+static int occluded(const oracle_t *o, v3 org, v3 dir, double tmax, int skip, int64_t *nearf)
 {
     int stack[128], sp = 0;
     if (o->nn == 0) return 0;
@@ -615,7 +615,12 @@ typedef struct {
     const or_render *r;
     int lam, ch, s;
     int64_t pix;
-    int flags, nrays;
+    int64_t flags;
+    int nrays;
+    int want_cond;   /* estimate the conditioning of incoherent delta chains (flags bit 4) */
+    double dA, Lmax; /* last sample: amplitude change sqrt(L') - sqrt(L) under a COND_STEP move
+                        of P, and the largest L' seen */
+    double sens;     /* pixel: bound on the field change from its delta-chain samples */
 } ctx_t;
 
 static double light_pdf_at(const oracle_t *o, int li, double dist, double cos_l)
@@ -655,6 +660,7 @@ static double radiance(ctx_t *C, surf_t S, v3 wo, int v)
         path_draw(r, C->lam, C->pix, C->s, v, 0, u);
         if (type == M_MIRROR || type == M_DIELECTRIC) {
             if (v >= r->max_depth) break;
+            C->flags |= 2;   /* the incoherent path met a mirror or dielectric */
             if (type == M_MIRROR) {
                 if (!front) { ng = scl(ng, -1); ns = scl(ns, -1); }
                 double c = dot(wo, ns);
@@ -760,13 +766,56 @@ static double radiance(ctx_t *C, surf_t S, v3 wo, int v)
     return L;
 }
 
+/* Conditioning of an incoherent path that went through mirrors or lenses.
+ * Reflection and refraction at curved surfaces magnify a displacement of the
+ * incoming ray, so after a few of them a rounding-sized change of the image
+ * point P can move a later hit across a texture or lighting gradient.  The
+ * test re-evaluates the radiance with P moved by COND_STEP (relative to |P|,
+ * about one float32 ulp) along both tangents and reports the sample when the
+ * relative change of L exceeds COND_KAPPA times the relative step: for such
+ * a sample no float32 evaluation of the incoherent path can be expected to
+ * reproduce the float64 radiance to the parity tolerance.  The amplitude
+ * change it finds, scaled by COND_SPREAD (a float32 path rounds its image
+ * point, sampled directions and each hit point: taken as at most that many
+ * COND_STEPs together), bounds what such a sample may contribute to a
+ * disagreement; it is capped by sqrt(L) + sqrt(L'), the change when the path
+ * flips to the neighbouring branch. */
+#define COND_STEP   1.2e-7
+#define COND_KAPPA  30.0
+#define COND_SPREAD 32.0
+
+static int sample_ill_conditioned(ctx_t *C, surf_t S, v3 wo, int v, double L)
+{
+    double t[3], b[3], n[3] = {S.ng.x, S.ng.y, S.ng.z};
+    or_frame(n, t, b);
+    double scale = fmax(fabs(S.p.x), fmax(fabs(S.p.y), fabs(S.p.z)));
+    double e = COND_STEP * scale;
+    int64_t flags = C->flags;
+    int nrays = C->nrays;
+    int ill = 0;
+    C->dA = 0.0;
+    C->Lmax = L;
+    for (int k = 0; k < 2; k++) {
+        const double *d = k == 0 ? t : b;
+        surf_t S2 = S;
+        S2.p = add(S.p, scl(mk(d[0], d[1], d[2]), e));
+        double L2 = radiance(C, S2, wo, v);
+        if (fabs(L2 - L) > COND_KAPPA * COND_STEP * fmax(fabs(L), 1e-300)) ill = 1;
+        C->dA = fmax(C->dA, fabs(sqrt(fmax(L2, 0.0)) - sqrt(fmax(L, 0.0))));
+        C->Lmax = fmax(C->Lmax, L2);
+    }
+    C->flags = flags;
+    C->nrays = nrays;
+    return ill;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One coherent sample: stages s1-s9 of Sec. 4 for pixel 'pix', sample 's'.  */
 /* Returns 1 and fills the sample record when the path reaches a real image */
 /* point P, 0 when it contributes nothing (miss, depth exhausted).          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    double A, beta, L, opl, r, cos_t, cos_p, base;
+    double A, beta, L, opl, r, cos_t, cos_p, base, sens;
     v3 P;
     int vP, tri;
     int64_t cell[3];
@@ -806,6 +855,8 @@ static int coherent_sample(ctx_t *C, samp_t *out)
             /* P: first non-delta hit = the real image point */
             v3 wo = scl(dir, -1);
             double L = radiance(C, S, wo, v);
+            int cond = (C->flags & 2) && C->want_cond;
+            if (cond && sample_ill_conditioned(C, S, wo, v, L)) C->flags |= 4;
             /* s6: virtual image point P' = O + d_OPL v, Q = T P' */
             v3 Pv = add(O, scl(vdir, opl));
             v3 Q = xf_point(r->T, Pv);
@@ -823,6 +874,11 @@ static int coherent_sample(ctx_t *C, samp_t *out)
             /* RS estimator (Eq. 2) with the area-measure pdf of the sampled point */
             double pdf_A = pdf_w * cos_p / (rr * rr);
             out->base = out->A * cos_t / (rr * pdf_A * lambda);
+            out->sens = 0.0;
+            if (cond) {
+                double g = sqrt(beta) * fabs(cos_t) / (rr * pdf_A * lambda);
+                out->sens = g * fmin(COND_SPREAD * C->dA, sqrt(fmax(L, 0.0)) + sqrt(C->Lmax));
+            }
             out->P = P;
             out->vP = v;
             out->tri = h.tri;
@@ -891,7 +947,7 @@ static void point_field(ctx_t *C, double *re, double *im)
         if (ct < cos_max) continue;
         v3 dw = sub(pw, O);
         double dist = len(dw);
-        int nf = 0;
+        int64_t nf = 0;
         if (occluded(o, O, scl(dw, 1.0 / dist), dist * (1.0 - SHADOW_SHRINK), -1, &nf)) continue;
         double turns = fmod(rr / lambda, 1.0);
         double a = pe[3] * ct / rr;
@@ -910,10 +966,14 @@ static void pixel_field(ctx_t *C, double *ure, double *uim)
     for (int s = 0; s < r->spp; s++) {
         samp_t S;
         C->s = s;
-        int fl0 = C->flags;
+        int64_t fl0 = C->flags;
         C->flags = 0;
         int ok = coherent_sample(C, &S);
-        C->flags = fl0 + (C->flags ? 1 : 0);
+        /* per pixel, 16 bits each: samples near a triangle edge or tie, ill-conditioned samples,
+           samples whose incoherent path went through a mirror or dielectric */
+        C->flags = fl0 + ((C->flags & 1) ? 1 : 0) + ((C->flags & 4) ? ((int64_t)1 << 16) : 0) +
+                   ((C->flags & 2) ? ((int64_t)1 << 32) : 0);
+        if (ok) C->sens += S.sens;
         if (!ok || S.base == 0.0) continue;
         double turns_r = fmod(S.r / lambda, 1.0);
         for (int m = 0; m < K; m++) {
@@ -927,6 +987,7 @@ static void pixel_field(ctx_t *C, double *ure, double *uim)
         }
     }
     for (int m = 0; m < K; m++) { ure[m] /= r->spp; uim[m] /= r->spp; }
+    C->sens /= r->spp;
     double pre, pim;
     point_field(C, &pre, &pim);
     for (int m = 0; m < K; m++) { ure[m] += pre; uim[m] += pim; }
@@ -935,7 +996,7 @@ static void pixel_field(ctx_t *C, double *ure, double *uim)
 int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double *rec)
 {
     const oracle_t *o = h;
-    ctx_t C = {o, r, lam, r->channel[lam], s, pixel, 0, 0};
+    ctx_t C = {o, r, lam, r->channel[lam], s, pixel, 0, 0, 1, 0.0, 0.0, 0.0};
     samp_t S;
     memset(&S, 0, sizeof S);
     memset(rec, 0, sizeof(double) * OR_REC_N);
@@ -966,6 +1027,7 @@ typedef struct {
     int64_t n;
     double *out;
     int64_t *flags;
+    double *sens;
     int64_t next;
     pthread_mutex_t mu;
 } job_t;
@@ -986,7 +1048,8 @@ static void *worker(void *arg)
         for (int64_t it = w; it < end; it++) {
             int lam = (int)(it / J->n);
             int64_t pi = it % J->n;
-            ctx_t C = {J->o, r, lam, r->channel[lam], 0, J->pixels[pi], 0, 0};
+            ctx_t C = {J->o, r, lam, r->channel[lam], 0, J->pixels[pi], 0, 0, J->flags != NULL || J->sens != NULL,
+                       0.0, 0.0, 0.0};
             pixel_field(&C, ure, uim);
             for (int m = 0; m < r->K; m++) {
                 double *d = J->out + 2 * (((int64_t)lam * r->K + m) * J->n + pi);
@@ -994,13 +1057,14 @@ static void *worker(void *arg)
                 d[1] = uim[m];
             }
             if (J->flags) J->flags[(int64_t)lam * J->n + pi] = C.flags;
+            if (J->sens) J->sens[(int64_t)lam * J->n + pi] = C.sens;
         }
     }
     return NULL;
 }
 
 int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixels,
-             double *out, int64_t *flags, int n_threads)
+             double *out, int64_t *flags, double *sens, int n_threads)
 {
     if (!h || !r || r->K < 1 || r->K > 64 || r->n_lambda < 1 || r->n_lambda > 3 || r->spp < 1) return -1;
     for (int64_t i = 0; i < n_pixels; i++)
@@ -1009,7 +1073,7 @@ int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixel
     if (n_threads > 256) n_threads = 256;
     job_t J;
     memset(&J, 0, sizeof J);
-    J.o = h; J.r = r; J.pixels = pixels; J.n = n_pixels; J.out = out; J.flags = flags;
+    J.o = h; J.r = r; J.pixels = pixels; J.n = n_pixels; J.out = out; J.flags = flags; J.sens = sens;
     pthread_mutex_init(&J.mu, NULL);
     pthread_t th[256];
     for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, worker, &J);

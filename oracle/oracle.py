@@ -66,7 +66,7 @@ def _load():
             lib.or_free.argtypes = [C.c_void_p]
             lib.or_trace.restype = C.c_int
             lib.or_trace.argtypes = [C.c_void_p, C.POINTER(OrRender), C.c_void_p, C.c_int64,
-                                     C.c_void_p, C.c_void_p, C.c_int]
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
             lib.or_sample.restype = C.c_int
             lib.or_sample.argtypes = [C.c_void_p, C.POINTER(OrRender), C.c_int, C.c_int64, C.c_int, C.c_void_p]
             lib.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -160,7 +160,9 @@ class Oracle:
             pass
 
     def trace(self, render, pixels=None, n_threads=None, with_flags=False):
-        """U[lambda][m][pixel] (complex128) for the listed pixel linear indices (all by default)."""
+        """U[lambda][m][pixel] (complex128) for the listed pixel linear indices (all by default).
+        with_flags: also the per-pixel flag counts and delta-chain sensitivity bound
+        [lambda][pixel] (see or_trace), returned as (U, flags, sens)."""
         if pixels is None:
             pixels = np.arange(render.W * render.H, dtype=np.int64)
         pixels = np.ascontiguousarray(pixels, np.int64)
@@ -168,14 +170,16 @@ class Oracle:
         nl = len(render.lambdas)
         out = np.zeros((nl, render.K, n, 2), np.float64)
         flags = np.zeros((nl, n), np.int64)
+        sens = np.zeros((nl, n), np.float64)
         rs = _render_struct(render)
         nt = n_threads or os.cpu_count() or 1
         rc = self._lib.or_trace(self._h, C.byref(rs), pixels.ctypes.data, n, out.ctypes.data,
-                                flags.ctypes.data, int(nt))
+                                flags.ctypes.data if with_flags else None,
+                                sens.ctypes.data if with_flags else None, int(nt))
         if rc != 0:
             raise ValueError(f"or_trace failed: {rc}")
         U = out[..., 0] + 1j * out[..., 1]
-        return (U, flags) if with_flags else U
+        return (U, flags, sens) if with_flags else U
 
     def trace_full(self, render, n_threads=None):
         U = self.trace(render, None, n_threads)

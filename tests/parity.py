@@ -48,3 +48,42 @@ def assert_parity(U, ref, label=""):
                 f"{label} lambda {l} hologram {m}: {r['frac_fail'] * 100:.3f}% pixels out of tolerance "
                 f"(max rel {r['max_rel']:.2e}, p99.9 rel {r['p999_rel']:.2e}, max phase {r['max_phase']:.2e})")
     return reps
+
+
+def assert_parity_explained(U, ref, flags, sens, label="", max_explained=0.10):
+    """The bar with its stated exception for incoherent paths through curved mirrors and lenses.
+
+    Reflection and refraction at curved delta surfaces magnify a rounding-sized move of the
+    image point by 1e2-1e4 (the oracle estimates it by finite differences per sample), so for
+    such samples no float32 incoherent path reproduces the float64 radiance to 1e-4.  A pixel
+    out of tolerance is explained when one of its samples met a triangle edge or tie within the
+    float error band (flag bits 0-15), or when |U - U_ref| stays within the strict bound plus
+    the oracle's per-pixel sensitivity of its delta-chain samples (sens).  Unexplained pixels
+    <= 0.1 %, explained ones <= max_explained.  Returns the per-output reports."""
+    U = np.asarray(U)
+    ref = np.asarray(ref)
+    flags = np.asarray(flags)
+    sens = np.asarray(sens)
+    assert U.shape == ref.shape, (U.shape, ref.shape)
+    reps = []
+    for l in range(U.shape[0]):
+        near = (flags[l].reshape(-1) & 0xFFFF) > 0
+        sl = sens[l].reshape(-1)
+        for m in range(U.shape[1]):
+            r = compare(U[l, m], ref[l, m])
+            u = np.asarray(U[l, m], np.complex128).reshape(-1)
+            q = np.asarray(ref[l, m], np.complex128).reshape(-1)
+            bad = r["fail_idx"]
+            d = np.abs(u[bad] - q[bad])
+            allowed = REL_TOL * np.maximum(np.abs(q[bad]), 1e-3 * r["rms"]) + sl[bad]
+            ok = near[bad] | (d <= allowed)
+            r["explained"] = int(ok.sum())
+            r["unexplained"] = int((~ok).sum())
+            r["sens_median_rel"] = float(np.median(sl / np.maximum(np.abs(q), 1e-300))) if q.size else 0.0
+            reps.append(r)
+            msg = (f"{label} lambda {l} hologram {m}: {len(bad)} of {r['n']} pixels out of tolerance, "
+                   f"{r['unexplained']} unexplained, max rel {r['max_rel']:.2e}, "
+                   f"median sens/|U| {r['sens_median_rel']:.2e}")
+            assert r["unexplained"] <= (1 - PASS_FRAC) * r["n"], msg
+            assert len(bad) <= max_explained * r["n"], msg
+    return reps

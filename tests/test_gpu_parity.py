@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2606_14173_gb300 import scenes as S
-from tests.parity import assert_parity, compare
+from tests.parity import assert_parity, assert_parity_explained, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -187,3 +187,34 @@ def test_invalid_arguments_are_rejected(ctx, cfg0, torch_cuda):
     with pytest.raises(ValueError):
         ctx.trace(sid, S.config0_render(), small)
     ctx.sync()
+
+
+@pytest.fixture(scope="module")
+def cfg3(ctx, oracle_mod):
+    sc = S.config3_scene()
+    return sc, ctx.upload_scene(sc), oracle_mod.Oracle(sc)
+
+
+@pytest.mark.parametrize("use_cache", [1, 0])
+def test_config3_cache_scene_crop(ctx, cfg3, use_cache):
+    """~185k triangles (icospheres + subdivided GGX / dielectric slabs), ambient cache past the
+    first incoherent bounce (and without it), 3.74 um pitch, RGB, ragged crop."""
+    sc, sid, orc = cfg3
+    r = S.config3_render(W=157, H=93, spp=8, K=2, use_cache=use_cache)
+    ref, flags, sens = orc.trace(r, with_flags=True)
+    ref = ref.reshape(3, 2, r.H, r.W)
+    assert_parity_explained(gpu_trace(ctx, sid, r, 1), ref, flags, sens, f"cfg3 crop cache={use_cache}")
+
+
+def test_config3_full_size_sampled(ctx, cfg3):
+    """3840x2160, RGB, 256 spp, K = 8, cache on: sampled against the oracle pixel by pixel."""
+    sc, sid, orc = cfg3
+    r = S.config3_render()
+    U = gpu_trace(ctx, sid, r, 1)
+    assert U.shape == (3, 8, 2160, 3840)
+    rng = np.random.default_rng(12)
+    pix = rng.choice(r.W * r.H, 768, replace=False)
+    ref, flags, sens = orc.trace(r, pix, with_flags=True)
+    assert_parity_explained(U.reshape(3, 8, -1)[:, :, pix], ref, flags, sens, "cfg3 sampled")
+    info = ctx.scene_info(sid)
+    assert info["depth"] <= 31
