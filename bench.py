@@ -35,6 +35,11 @@ ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 # algorithmic FP32 work per counted event (see the design notes): two child-box slab tests per
 # node visit are counted as two box tests
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
+# DRAM bytes (read + write) per k_trace launch, averaged over every k_trace launch of one frame of
+# the 1920x270 band of the 30-sphere scene (same wave size as the full 1080p frame) in one ncu
+# capture; the summary and its command are in profiles/k_trace_dram_band_1920x270.md.  Set to
+# None whenever k_trace changes until it is captured again.
+TRACE_DRAM_BYTES_PER_LAUNCH = None
 
 
 # name -> (description, scene factory, render factory)
@@ -88,7 +93,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def window(self, t_begin, t_end):
+        """Keep the samples taken between t_begin and t_end (perf_counter seconds) only: the
+        sampler starts before the warm-up so that its own start-up overlaps no timed step."""
+        self.t_window = (t_begin, t_end)
 
     def stop(self):
         if self.proc is None:
@@ -101,7 +111,10 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        tw = getattr(self, "t_window", None)
+        for t, r in self.rows:
+            if tw is not None and not (tw[0] - 0.2 <= t <= tw[1] + 0.2):
+                continue
             try:
                 sm.append(float(r[1]))
                 mx.append(float(r[2]))
@@ -291,14 +304,15 @@ def main():
             ctx.trace(sid, rp, op, precision=hpt.PREC_FP64, stream=stream)
 
     def timed(step, k, w, sample_clocks=False):
+        clk = ClockSampler(local)
+        if sample_clocks:
+            clk.start()
         for _ in range(w):
             step()
         ctx.sync()
         barrier(world)
         torch.cuda.synchronize()
-        clk = ClockSampler(local)
-        if sample_clocks:
-            clk.start()
+        th0 = time.perf_counter()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k)]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -310,7 +324,9 @@ def main():
             ev[2 * i + 1].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
+        th1 = time.perf_counter()
         barrier(world)
+        clk.window(th0, th1)
         clocks = clk.stop() if sample_clocks else None
         ctx.sync()
         total_ms = t0.elapsed_time(t1)
@@ -347,21 +363,30 @@ def main():
                "d2h_bytes_per_step": int(host.nbytes),
                "api": "hpt_trace_host (device trace + D2H copy of all K x 3 fields into pinned host memory)"}
 
-    # roofline of the trace kernel: algorithmic FP32 work from the per-sample work counters
+    # roofline of the dominant kernel (k_trace): its algorithmic FP32 work per frame from the work
+    # counters, over its own device time per frame from CUDA events around every launch
     if args.no_counters:
         cnt = {"samples": 1, "box_tests": 0, "tri_tests": 0, "refines": 0, "shadow_rays": 0, "bounces": 0}
+        kt = {k: (1.0, 1) for k in hpt.KERNEL_NAMES}
     else:
         cnt = ctx.trace_counters(sid, r, out, precision=hpt.PREC_DF32)
+        kt = ctx.trace_timed(sid, r, out, precision=hpt.PREC_DF32)
     ns = max(cnt["samples"], 1)
     vertices = cnt["shadow_rays"] + cnt["bounces"] + cnt["refines"]
-    flops = (cnt["box_tests"] * FLOP_PER["box_tests"] + cnt["tri_tests"] * FLOP_PER["tri_tests"]
-             + cnt["refines"] * FLOP_PER["refines"] + vertices * FLOP_PER["vertex"]
-             + ns * r.K * FLOP_PER["hologram"])
-    avg_launch_s = statistics.mean(launch_ms) / 1e3
-    achieved = flops / avg_launch_s / 1e12
+    trace_flops = (cnt["box_tests"] * FLOP_PER["box_tests"] + cnt["tri_tests"] * FLOP_PER["tri_tests"]
+                   + cnt["refines"] * FLOP_PER["refines"])
+    flops = trace_flops + vertices * FLOP_PER["vertex"] + ns * r.K * FLOP_PER["hologram"]
+    trace_ms, trace_launches = kt["k_trace"]
+    achieved = trace_flops / (trace_ms / 1e3) / 1e12
+    kern_total = sum(ms for ms, _ in kt.values())
+    traffic = TRACE_DRAM_BYTES_PER_LAUNCH if args.workload in ("cfg2", "band") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_trace",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+                "launches_per_frame": trace_launches, "ms_per_launch": trace_ms / max(trace_launches, 1),
+                "flop_per_launch": trace_flops / max(trace_launches, 1),
+                "kernel_share": {k: ms / kern_total for k, (ms, _) in kt.items()},
+                "whole_path_tflops": flops / statistics.mean([x / 1e3 for x in launch_ms]) / 1e12,
                 "per_sample": {k: v / ns for k, v in cnt.items() if k != "samples"},
                 "flops_per_sample": flops / ns}
 
@@ -387,7 +412,9 @@ def main():
                            "path_samples_per_step": samples_per_step, "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MiB write)"},
                 "holograms_per_s": holo_per_s, "plain_fp64": plain, "launch_ms": launch_ms,
-                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "serving": serving,
+                "idle_ms_per_step": (total_ms - sum(launch_ms)) / args.steps,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * sum(n for _, n in kt.values()),
+                "graph_launches": args.steps, "roofline": roofline, "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

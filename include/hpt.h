@@ -189,6 +189,18 @@ enum { HPT_NCOUNTERS = 8 };
 hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                               void *out_dev, size_t out_bytes, uint64_t counters[HPT_NCOUNTERS]);
 
+/* Trace one frame like hpt_trace, without a captured graph, with a CUDA event recorded on the
+ * context's wave stream before every launch, and report the device time and number of kernel
+ * launches per kernel kind: HPT_K_GEN (primary path generation, with the queue-counter reset),
+ * HPT_K_TRACE (BVH traversal of one queue iteration), HPT_K_SHADE (coherent and incoherent
+ * shading of one iteration: two launches), HPT_K_ACCUM (Path-Reuse accumulation, Eq. 5).
+ * Synchronous; the results in out_dev equal those of hpt_trace.  The paper has no counterpart:
+ * this feeds the roofline of each kernel. */
+enum { HPT_K_GEN = 0, HPT_K_TRACE = 1, HPT_K_SHADE = 2, HPT_K_ACCUM = 3, HPT_NKERNELS = 4 };
+hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
+                           void *out_dev, size_t out_bytes, float kernel_ms[HPT_NKERNELS],
+                           uint32_t launches[HPT_NKERNELS]);
+
 /* Choose the context's wave size (paths per wave: 1M .. 16M, within half of the free HBM) by
  * timing hpt_trace of a 128-row band of 'desc' (spp capped at 32) for each candidate; keeps the
  * fastest (a larger wave must win by more than 2 %), reallocates the wave state and drops the

@@ -617,9 +617,9 @@ typedef struct {
     int64_t pix;
     int64_t flags;
     int nrays;
-    int want_cond;   /* estimate the conditioning of incoherent delta chains (flags bit 4) */
-    double dA, Lmax; /* last sample: amplitude change sqrt(L') - sqrt(L) under a COND_STEP move
-                        of P, and the largest L' seen */
+    int want_cond;   /* estimate the conditioning of the incoherent part (flags bit 4, sens) */
+    double dA, Lmax; /* last sample: bound on |sqrt(L') - sqrt(L)| under float32-sized moves of
+                        P, and the largest L' the probes saw */
     double sens;     /* pixel: bound on the field change from its delta-chain samples */
 } ctx_t;
 
@@ -766,20 +766,24 @@ static double radiance(ctx_t *C, surf_t S, v3 wo, int v)
     return L;
 }
 
-/* Conditioning of an incoherent path that went through mirrors or lenses.
- * Reflection and refraction at curved surfaces magnify a displacement of the
- * incoming ray, so after a few of them a rounding-sized change of the image
- * point P can move a later hit across a texture or lighting gradient.  The
- * test re-evaluates the radiance with P moved by COND_STEP (relative to |P|,
- * about one float32 ulp) along both tangents and reports the sample when the
- * relative change of L exceeds COND_KAPPA times the relative step: for such
- * a sample no float32 evaluation of the incoherent path can be expected to
- * reproduce the float64 radiance to the parity tolerance.  The amplitude
- * change it finds, scaled by COND_SPREAD (a float32 path rounds its image
- * point, sampled directions and each hit point: taken as at most that many
- * COND_STEPs together), bounds what such a sample may contribute to a
- * disagreement; it is capped by sqrt(L) + sqrt(L'), the change when the path
- * flips to the neighbouring branch. */
+/* Conditioning of the incoherent part of a sample.
+ * The incoherent radiance L(P) is evaluated in float32 by a fast path, so the
+ * question is how much a rounding-sized change of the image point P moves L.
+ * Mostly it barely does, but reflection and refraction at curved mirrors and
+ * lenses (and near-specular GGX) magnify a displacement of the incoming ray,
+ * so after a few of them a later hit can move across a texture or lighting
+ * gradient, or the path can change branch.  Two probes, with the same random
+ * numbers:
+ *   - P moved by COND_STEP (relative to |P|, about one float32 ulp) along both
+ *     tangents: the local sensitivity; the sample is ill-conditioned when the
+ *     relative change of L exceeds COND_KAPPA times the relative step;
+ *   - P moved by COND_SPREAD steps the other way along both tangents: branch
+ *     changes within the reach of float32 rounding, which the local probe misses.
+ * The amplitude change sqrt(L') - sqrt(L), the local one scaled by COND_SPREAD
+ * (a float32 path rounds its image point, its sampled directions and every hit
+ * point: taken as at most that many steps together), bounds what the sample
+ * may contribute to a disagreement; it is capped by sqrt(L) + sqrt(L'max),
+ * the change when the path flips to the neighbouring branch. */
 #define COND_STEP   1.2e-7
 #define COND_KAPPA  30.0
 #define COND_SPREAD 32.0
@@ -789,21 +793,27 @@ static int sample_ill_conditioned(ctx_t *C, surf_t S, v3 wo, int v, double L)
     double t[3], b[3], n[3] = {S.ng.x, S.ng.y, S.ng.z};
     or_frame(n, t, b);
     double scale = fmax(fabs(S.p.x), fmax(fabs(S.p.y), fabs(S.p.z)));
-    double e = COND_STEP * scale;
     int64_t flags = C->flags;
     int nrays = C->nrays;
     int ill = 0;
-    C->dA = 0.0;
+    double dlin = 0.0, dbig = 0.0, a0 = sqrt(fmax(L, 0.0));
     C->Lmax = L;
-    for (int k = 0; k < 2; k++) {
-        const double *d = k == 0 ? t : b;
+    for (int k = 0; k < 4; k++) {
+        const double *d = (k & 1) ? b : t;
+        const double e = k < 2 ? COND_STEP * scale : -COND_SPREAD * COND_STEP * scale;
         surf_t S2 = S;
         S2.p = add(S.p, scl(mk(d[0], d[1], d[2]), e));
         double L2 = radiance(C, S2, wo, v);
-        if (fabs(L2 - L) > COND_KAPPA * COND_STEP * fmax(fabs(L), 1e-300)) ill = 1;
-        C->dA = fmax(C->dA, fabs(sqrt(fmax(L2, 0.0)) - sqrt(fmax(L, 0.0))));
+        double da = fabs(sqrt(fmax(L2, 0.0)) - a0);
+        if (k < 2) {
+            if (fabs(L2 - L) > COND_KAPPA * COND_STEP * fmax(fabs(L), 1e-300)) ill = 1;
+            dlin = fmax(dlin, COND_SPREAD * da);
+        } else {
+            dbig = fmax(dbig, da);
+        }
         C->Lmax = fmax(C->Lmax, L2);
     }
+    C->dA = fmax(dlin, dbig);
     C->flags = flags;
     C->nrays = nrays;
     return ill;
@@ -855,7 +865,7 @@ static int coherent_sample(ctx_t *C, samp_t *out)
             /* P: first non-delta hit = the real image point */
             v3 wo = scl(dir, -1);
             double L = radiance(C, S, wo, v);
-            int cond = (C->flags & 2) && C->want_cond;
+            int cond = C->want_cond;
             if (cond && sample_ill_conditioned(C, S, wo, v, L)) C->flags |= 4;
             /* s6: virtual image point P' = O + d_OPL v, Q = T P' */
             v3 Pv = add(O, scl(vdir, opl));
@@ -877,7 +887,7 @@ static int coherent_sample(ctx_t *C, samp_t *out)
             out->sens = 0.0;
             if (cond) {
                 double g = sqrt(beta) * fabs(cos_t) / (rr * pdf_A * lambda);
-                out->sens = g * fmin(COND_SPREAD * C->dA, sqrt(fmax(L, 0.0)) + sqrt(C->Lmax));
+                out->sens = g * fmin(C->dA, sqrt(fmax(L, 0.0)) + sqrt(C->Lmax));
             }
             out->P = P;
             out->vP = v;

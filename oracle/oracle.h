@@ -66,13 +66,13 @@ void *or_build(const or_scene *s);
 void or_free(void *h);
 /* out: [n_lambda][K][n_pixels][2] complex128.  flags (optional): [n_lambda][n_pixels], three
  * 16-bit sample counts: bits 0-15 samples with a ray query near a triangle edge or tie; bits
- * 16-31 samples whose incoherent path is ill-conditioned (a rounding-sized move of the image
+ * 16-31 samples whose incoherent part is ill-conditioned (a rounding-sized move of the image
  * point changes its radiance by more than 30x as much, relatively); bits 32-47 samples whose
  * incoherent path met a mirror or dielectric.  sens (optional): [n_lambda][n_pixels], a bound
- * on how far float32 rounding in those delta-chain samples can move |U_m| (the same for every
- * m; the phase of a sample does not depend on its radiance).  Conditioning is only estimated
- * when flags or sens are requested.  or_sample's record flags: bit 0 near edge, bit 1 delta in
- * the incoherent path, bit 2 ill-conditioned.  Returns 0 or <0. */
+ * on how far float32-sized moves of the image points can change |U_m| (the same for every m;
+ * the phase of a sample does not depend on its radiance).  Conditioning is only estimated
+ * when flags or sens are requested.  or_sample's record flags: bit 0 near edge, bit 1 delta
+ * in the incoherent path, bit 2 ill-conditioned.  Returns 0 or <0. */
 int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixels,
              double *out, int64_t *flags, double *sens, int n_threads);
 int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double *rec);

@@ -239,19 +239,33 @@ struct hpt_ctx {
     int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
     // captured frames of hpt_trace, keyed by what fixes the launch sequence
+    // A captured frame reads its job table from d_table; each replay first copies the
+    // caller's descriptor there from one of TABLE_RING pinned buffers, so the host only waits
+    // when it runs TABLE_RING copies ahead of the device.
+    static constexpr int TABLE_RING = 4;
     struct FrameGraph {
         int prec = 0, spp = 0, max_depth = 0, capacity = 0;
         long long n_items = 0;
         void *out = nullptr;
-        JobTable *d_table = nullptr, *h_table = nullptr;
+        JobTable *d_table = nullptr;
+        JobTable *h_ring[TABLE_RING] = {};
+        cudaEvent_t copied[TABLE_RING] = {};
+        bool ring_used[TABLE_RING] = {};
+        int ring_next = 0;
         cudaGraphExec_t exec = nullptr;
         cudaEvent_t done = nullptr;
-        bool used = false;
         uint64_t last_use = 0;
     };
     std::vector<FrameGraph> graphs;
     bool use_graphs = true;
     uint64_t graph_clock = 0;
+    // per-kernel timing (hpt_trace_timed): an event before every launch of a wave, one kind each
+    struct KernelTimer {
+        std::vector<cudaEvent_t> ev;
+        std::vector<int> kind;
+        size_t used = 0;
+    };
+    KernelTimer *timer = nullptr;
     SlotScratch *d_scr = nullptr;
     cudaStream_t wstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -359,6 +373,8 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     return HPT_OK;
 }
 
+static void free_frame(hpt_ctx::FrameGraph &g);
+
 extern "C" void hpt_destroy(hpt_ctx *ctx)
 {
     if (!ctx) return;
@@ -371,12 +387,7 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto &w : ctx->inflight) cudaEventDestroy(w.ev);
-    for (auto &g : ctx->graphs) {
-        cudaGraphExecDestroy(g.exec);
-        cudaEventDestroy(g.done);
-        cudaFree(g.d_table);
-        cudaFreeHost(g.h_table);
-    }
+    for (auto &g : ctx->graphs) free_frame(g);
     for (auto e : ctx->free_events) cudaEventDestroy(e);
     for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
     for (auto &s : ctx->slots) {
@@ -844,16 +855,34 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     memset(&wd, 0, sizeof wd);
     int max_depth = 1;
     hpt_status st = HPT_OK;
+    auto mark = [&](int kind) -> cudaError_t {
+        hpt_ctx::KernelTimer *tm = ctx->timer;
+        if (!tm) return cudaSuccess;
+        if (tm->used == tm->ev.size()) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            tm->ev.push_back(e);
+            tm->kind.push_back(0);
+        }
+        tm->kind[tm->used] = kind;
+        return cudaEventRecord(tm->ev[tm->used++], ws);
+    };
     auto flush = [&]() -> hpt_status {
         if (wd.n_seg == 0) return HPT_OK;
         const int n_iter = max_depth + 1;
+        CUDA_TRY(mark(HPT_K_GEN));
         CUDA_TRY(cudaMemsetAsync(ctx->d_scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws));
         CUDA_TRY(wave_gen(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
         for (int it = 0; it < n_iter; ++it) {
+            CUDA_TRY(mark(HPT_K_TRACE));
             CUDA_TRY(wave_trace(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_trace[prec], ws));
+            CUDA_TRY(mark(HPT_K_SHADE));
             CUDA_TRY(wave_shade(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws));
         }
+        CUDA_TRY(mark(HPT_K_ACCUM));
         CUDA_TRY(wave_accum(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        CUDA_TRY(mark(-1));
         if (allow_debug && ctx->debug_waves > 0) {
             // diagnostic: queue lengths per iteration of the first waves (HPT_DEBUG_WAVES=n)
             --ctx->debug_waves;
@@ -920,9 +949,22 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
 }
 
 // A frame of one job as a captured CUDA graph: the first call with a given launch shape
-// (arithmetic, output buffer, items, spp, depth, wave capacity) captures the job-table upload
-// and every wave launch; later calls refresh the pinned job table and replay.  Caller holds
+// (arithmetic, output buffer, items, spp, depth, wave capacity) captures every wave launch;
+// each call copies its job table to the frame's device table and replays.  Caller holds
 // ctx->mu.
+static void free_frame(hpt_ctx::FrameGraph &g)
+{
+    if (g.done) cudaEventSynchronize(g.done);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.done) cudaEventDestroy(g.done);
+    for (int k = 0; k < hpt_ctx::TABLE_RING; ++k) {
+        if (g.copied[k]) cudaEventDestroy(g.copied[k]);
+        if (g.h_ring[k]) cudaFreeHost(g.h_ring[k]);
+    }
+    if (g.d_table) cudaFree(g.d_table);
+    g = hpt_ctx::FrameGraph();
+}
+
 static hpt_status run_graph(hpt_ctx *ctx, const DevJob &J, int prec, cudaStream_t user)
 {
     hpt_status st = ensure_paths(ctx);
@@ -940,11 +982,7 @@ static hpt_status run_graph(hpt_ctx *ctx, const DevJob &J, int prec, cudaStream_
                                         [](const hpt_ctx::FrameGraph &a, const hpt_ctx::FrameGraph &b) {
                                             return a.last_use < b.last_use;
                                         });
-            cudaEventSynchronize(lru->done);
-            cudaGraphExecDestroy(lru->exec);
-            cudaEventDestroy(lru->done);
-            cudaFree(lru->d_table);
-            cudaFreeHost(lru->h_table);
+            free_frame(*lru);
             ctx->graphs.erase(lru);
         }
         hpt_ctx::FrameGraph x;
@@ -954,42 +992,43 @@ static hpt_status run_graph(hpt_ctx *ctx, const DevJob &J, int prec, cudaStream_
         x.spp = J.spp;
         x.max_depth = J.max_depth;
         x.capacity = ctx->capacity;
-        CUDA_TRY(cudaMalloc(&x.d_table, sizeof(JobTable)));
-        CUDA_TRY(cudaMallocHost(&x.h_table, sizeof(JobTable)));
-        CUDA_TRY(cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming));
-        x.h_table->n_jobs = 1;
-        x.h_table->jobs[0] = J;
+        cudaError_t e0 = cudaMalloc(&x.d_table, sizeof(JobTable));
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming);
+        for (int k = 0; k < hpt_ctx::TABLE_RING && e0 == cudaSuccess; ++k) {
+            e0 = cudaMallocHost(&x.h_ring[k], sizeof(JobTable));
+            if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&x.copied[k], cudaEventDisableTiming);
+        }
+        if (e0 != cudaSuccess) {
+            free_frame(x);
+            return fail(HPT_ERR_CUDA, "frame resources: %s", cudaGetErrorString(e0));
+        }
         cudaGraph_t graph = nullptr;
         CUDA_TRY(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = cudaMemcpyAsync(x.d_table, x.h_table, bytes, cudaMemcpyHostToDevice, ws);
-        hpt_status st2 = e1 == cudaSuccess ? enqueue_waves(ctx, &J, 1, prec, false, x.d_table, ws, false) : HPT_ERR_CUDA;
+        hpt_status st2 = enqueue_waves(ctx, &J, 1, prec, false, x.d_table, ws, false);
         cudaError_t e2 = cudaStreamEndCapture(ws, &graph);
-        if (e1 != cudaSuccess || st2 || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaFree(x.d_table);
-            cudaFreeHost(x.h_table);
-            cudaEventDestroy(x.done);
-            return st2 ? st2 : fail(HPT_ERR_CUDA, "frame capture failed: %s", cudaGetErrorString(e1 ? e1 : e2));
-        }
-        cudaError_t e3 = cudaGraphInstantiate(&x.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e3 != cudaSuccess) {
-            cudaFree(x.d_table);
-            cudaFreeHost(x.h_table);
-            cudaEventDestroy(x.done);
-            return fail(HPT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+        cudaError_t e3 = cudaErrorUnknown;
+        if (!st2 && e2 == cudaSuccess) e3 = cudaGraphInstantiate(&x.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st2 || e2 != cudaSuccess || e3 != cudaSuccess) {
+            free_frame(x);
+            return st2 ? st2 : fail(HPT_ERR_CUDA, "frame capture failed: %s", cudaGetErrorString(e2 ? e2 : e3));
         }
         ctx->graphs.push_back(x);
         g = &ctx->graphs.back();
-    } else {
-        // the graph's copy reads the pinned table when it runs: wait for the previous replay
-        if (g->used) CUDA_TRY(cudaEventSynchronize(g->done));
-        g->h_table->jobs[0] = J;
     }
-    g->used = true;
+    // this replay's job table: a free pinned ring buffer, copied ahead of the replay on ws
+    const int k = g->ring_next;
+    g->ring_next = (k + 1) % hpt_ctx::TABLE_RING;
+    if (g->ring_used[k]) CUDA_TRY(cudaEventSynchronize(g->copied[k]));
+    g->ring_used[k] = true;
+    g->h_ring[k]->n_jobs = 1;
+    g->h_ring[k]->pad = 0;
+    g->h_ring[k]->jobs[0] = J;
     g->last_use = ++ctx->graph_clock;
     CUDA_TRY(cudaEventRecord(ctx->ev_in, user));
     CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
+    CUDA_TRY(cudaMemcpyAsync(g->d_table, g->h_ring[k], bytes, cudaMemcpyHostToDevice, ws));
+    CUDA_TRY(cudaEventRecord(g->copied[k], ws));
     CUDA_TRY(cudaGraphLaunch(g->exec, ws));
     CUDA_TRY(cudaEventRecord(g->done, ws));
     CUDA_TRY(cudaEventRecord(ctx->ev_out, ws));
@@ -1085,16 +1124,46 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
     return read_status(ctx);
 }
 
+extern "C" hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_dev,
+                                      size_t out_bytes, float kernel_ms[HPT_NKERNELS],
+                                      uint32_t launches[HPT_NKERNELS])
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_dev || !kernel_ms || !launches) return fail(HPT_ERR_INVALID_ARG, "out_dev, kernel_ms or launches is NULL");
+    DevJob J;
+    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    hpt_ctx::KernelTimer tm;
+    ctx->timer = &tm;
+    st = run_jobs(ctx, &J, 1, desc->precision, false, 0);
+    ctx->timer = nullptr;
+    cudaError_t e = cudaStreamSynchronize(ctx->wstream);
+    for (int k = 0; k < HPT_NKERNELS; ++k) kernel_ms[k] = 0.0f, launches[k] = 0;
+    if (!st && e == cudaSuccess) {
+        // shade launches the coherent and the incoherent kernel back to back
+        static const uint32_t per_call[HPT_NKERNELS] = {1, 1, 2, 1};
+        for (size_t i = 0; i + 1 < tm.used && e == cudaSuccess; ++i) {
+            const int k = tm.kind[i];
+            if (k < 0) continue;
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]);
+            kernel_ms[k] += ms;
+            launches[k] += per_call[k];
+        }
+    }
+    for (cudaEvent_t x : tm.ev) cudaEventDestroy(x);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(HPT_ERR_CUDA, "kernel timing: %s", cudaGetErrorString(e));
+    return read_status(ctx);
+}
+
 // ---------------------------------------------------------------------------- autotune
 static void drop_graphs(hpt_ctx *ctx)
 {
-    for (auto &g : ctx->graphs) {
-        cudaEventSynchronize(g.done);
-        cudaGraphExecDestroy(g.exec);
-        cudaEventDestroy(g.done);
-        cudaFree(g.d_table);
-        cudaFreeHost(g.h_table);
-    }
+    for (auto &g : ctx->graphs) free_frame(g);
     ctx->graphs.clear();
 }
 

@@ -24,7 +24,11 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 # exported symbols, as declared in include/hpt.h
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
-           "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune"]
+           "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed"]
+
+
+# kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
+KERNEL_NAMES = ["k_gen", "k_trace", "k_shade", "k_accum"]
 
 
 class HptError(RuntimeError):
@@ -82,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_trace_timed.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_uint32)]
     lib.hpt_submit.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
     lib.hpt_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
     lib.hpt_wait.argtypes = [vp, C.c_uint64, C.c_uint32]
@@ -227,6 +233,15 @@ class Context:
         c = (C.c_uint64 * NCOUNTERS)()
         _check(self.lib.hpt_trace_counters(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, c))
         return dict(zip(COUNTER_NAMES, [int(x) for x in c]))
+
+    def trace_timed(self, sid: int, r, out, precision=PREC_DF32):
+        """One frame with CUDA events around every launch: {kernel: (device ms, launches)}."""
+        ptr, nbytes = _dev_buffer(out, r)
+        d = render_desc(r, precision)
+        ms = (C.c_float * len(KERNEL_NAMES))()
+        n = (C.c_uint32 * len(KERNEL_NAMES))()
+        _check(self.lib.hpt_trace_timed(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, ms, n))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
 
     def autotune(self, sid: int, r, precision=PREC_DF32) -> int:
         """Pick the wave size by timing a band of this render; returns paths per wave."""

@@ -43,6 +43,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", offsetof(hpt_scene_desc, tex_floats), offsetof(hpt_scene_desc, cache_res),
          offsetof(hpt_scene_desc, cache_E), offsetof(hpt_render_desc, seed), offsetof(hpt_render_desc, T));
   printf("%zu %zu\n", offsetof(hpt_render_desc, precision), offsetof(hpt_render_desc, use_cache));
+  printf("%d %d %d %d\n", HPT_NCOUNTERS, HPT_NKERNELS, HPT_K_TRACE, HPT_K_ACCUM);
   return 0;
 }
 '''
@@ -56,7 +57,8 @@ int main(void) {
     got = [C.sizeof(hpt.Material), C.sizeof(hpt.SceneDesc), C.sizeof(hpt.RenderDesc), C.sizeof(hpt.CtxDesc),
            hpt.SceneDesc.tex_floats.offset, hpt.SceneDesc.cache_res.offset, hpt.SceneDesc.cache_E.offset,
            hpt.RenderDesc.seed.offset, hpt.RenderDesc.T.offset, hpt.RenderDesc.precision.offset,
-           hpt.RenderDesc.use_cache.offset]
+           hpt.RenderDesc.use_cache.offset, hpt.NCOUNTERS, len(hpt.KERNEL_NAMES),
+           hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum")]
     assert [int(x) for x in out] == got
 
 

@@ -58,3 +58,53 @@ def test_autotune_keeps_results(torch_cuda):
         assert np.array_equal(before, after)
     finally:
         ctx.close()
+
+
+def test_back_to_back_replays_keep_their_own_job_tables(torch_cuda):
+    """Six replays of one captured frame queued without a host wait, each with another seed: each
+    replay must read its own job table (the tables go through a ring of pinned buffers)."""
+    from paper_2606_14173_gb300 import hpt
+    torch = torch_cuda
+    direct = hpt.Context(0, graphs=False)
+    graphed = hpt.Context(0, graphs=True)
+    try:
+        sc = S.config1_scene()
+        sd, sg = direct.upload_scene(sc), graphed.upload_scene(sc)
+        r = S.config1_render(W=160, H=90, spp=4, K=2)
+        out = hpt.alloc_output(r)
+        stream = torch.cuda.current_stream()
+        copies = []
+        for seed in range(1, 7):
+            r.seed = seed
+            graphed.trace(sg, r, out, precision=1, stream=stream)
+            copies.append(out.clone())          # same stream: ordered after this replay
+        graphed.sync()
+        torch.cuda.synchronize()
+        od = hpt.alloc_output(r)
+        for seed, c in zip(range(1, 7), copies):
+            r.seed = seed
+            assert np.array_equal(c.cpu().numpy(), _trace(direct, sd, r, od)), seed
+    finally:
+        direct.close()
+        graphed.close()
+
+
+def test_timed_trace_reports_kernels_and_keeps_results(torch_cuda):
+    from paper_2606_14173_gb300 import hpt
+    ctx = hpt.Context(0)
+    try:
+        sid = ctx.upload_scene(S.config1_scene())
+        r = S.config1_render(W=320, H=180, spp=8, K=2)
+        out = hpt.alloc_output(r)
+        ref = _trace(ctx, sid, r, out)
+        out.zero_()
+        t = ctx.trace_timed(sid, r, out)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert set(t) == set(hpt.KERNEL_NAMES)
+        waves = t["k_gen"][1]
+        assert waves >= 1 and t["k_accum"][1] == waves
+        assert t["k_trace"][1] == waves * (r.max_depth + 1)
+        assert t["k_shade"][1] == 2 * t["k_trace"][1]
+        assert all(ms > 0 for ms, _ in t.values())
+    finally:
+        ctx.close()
