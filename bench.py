@@ -95,6 +95,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
+    def wait_ready(self, timeout=20.0):
+        """Block until the first sample arrived: nvidia-smi's start-up (NVML initialisation) can
+        hold the GPU for a fraction of a second, which must not fall into a timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.rows and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
+
     def window(self, t_begin, t_end):
         """Keep the samples taken between t_begin and t_end (perf_counter seconds) only: the
         sampler starts before the warm-up so that its own start-up overlaps no timed step."""
@@ -307,6 +314,7 @@ def main():
         clk = ClockSampler(local)
         if sample_clocks:
             clk.start()
+            clk.wait_ready()
         for _ in range(w):
             step()
         ctx.sync()
