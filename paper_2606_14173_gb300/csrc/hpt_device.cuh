@@ -126,9 +126,15 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     const float4 *__restrict__ tris = sc.tri4;
     int sp = 0;
     int node = 0;
+    // Speculative descent (Aila and Laine 2009): a leaf met while none is pending is postponed
+    // and the descent continues until every active lane of the warp holds a leaf; then the
+    // lanes test their leaves together.  Culling uses the closest hit known so far, so only the
+    // order of the visits changes: the closest hit (ties to the lower id) is the same, and the
+    // candidates of a coherent ray, re-decided exactly, lead to the same decision.
+    const int SENT = 0x7FFFFFFF;    // stack exhausted
+    int LEAF = 0;                   // pending leaf (< 0); 0 = none (the root is never a leaf)
     for (;;) {
-        // descend inner nodes
-        while (node >= 0) {
+        while (node >= 0 && node != SENT) {
             const float4 *np = nodes + 4 * node;
             float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
             float tl = h.t * cull;
@@ -146,8 +152,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
             bool h0 = c0min <= c0max, h1 = c1min <= c1max;
             int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
             if (!h0 && !h1) {
-                if (sp == 0) return h.tri >= 0;
-                node = stk[(--sp) * SSTRIDE];
+                node = sp > 0 ? stk[(--sp) * SSTRIDE] : SENT;
             } else {
                 node = h0 ? l0 : l1;
                 if (h0 && h1) {
@@ -157,45 +162,56 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
                     else status |= ST_STACK_OVERFLOW;
                 }
             }
+            if (node < 0 && LEAF == 0) {
+                LEAF = node;
+                node = sp > 0 ? stk[(--sp) * SSTRIDE] : SENT;
+            }
+            if (!__any_sync(__activemask(), LEAF == 0)) break;
         }
-        // leaf: ~(start << 8 | count)
-        int code = ~node;
-        int start = code >> 8, count = code & 255;
-        for (int i = start; i < start + count; ++i) {
-            const float4 *tp = tris + 3 * i;
-            float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
-            int id = __float_as_int(A.w);
-            if (STATS) cnt.tris++;
-            if (id == skip) continue;
-            float3 e1 = xyz(E1), e2 = xyz(E2);
-            float3 pv = cross3(d, e2);
-            float det = dot3(e1, pv);
-            float idet = __fdividef(1.0f, det);
-            float3 tv = o - xyz(A);
-            float u = dot3(tv, pv) * idet;
-            float3 qv = cross3(tv, e1);
-            float v = dot3(d, qv) * idet;
-            float t = dot3(e2, qv) * idet;
-            if (TRACK) {
-                const float m = fminf(fminf(u, v), 1.0f - u - v);
-                if (fabsf(m) < NEAR_MARGIN && t > 0.0f && t <= h.t * (1.0f + 10.0f * TIE_REL)) cand.add(t, id);
+        while (LEAF < 0) {
+            // leaf: ~(start << 8 | count)
+            int code = ~LEAF;
+            int start = code >> 8, count = code & 255;
+            for (int i = start; i < start + count; ++i) {
+                const float4 *tp = tris + 3 * i;
+                float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
+                int id = __float_as_int(A.w);
+                if (STATS) cnt.tris++;
+                if (id == skip) continue;
+                float3 e1 = xyz(E1), e2 = xyz(E2);
+                float3 pv = cross3(d, e2);
+                float det = dot3(e1, pv);
+                float idet = __fdividef(1.0f, det);
+                float3 tv = o - xyz(A);
+                float u = dot3(tv, pv) * idet;
+                float3 qv = cross3(tv, e1);
+                float v = dot3(d, qv) * idet;
+                float t = dot3(e2, qv) * idet;
+                if (TRACK) {
+                    const float m = fminf(fminf(u, v), 1.0f - u - v);
+                    if (fabsf(m) < NEAR_MARGIN && t > 0.0f && t <= h.t * (1.0f + 10.0f * TIE_REL)) cand.add(t, id);
+                }
+                bool inside = (u >= -eps_w) && (v >= -eps_w) && (u + v <= 1.0f + eps_w) && (t > 0.0f);
+                if (!inside) continue;
+                if (ANYHIT) {
+                    if (t < tmax) { h.t = t; h.tri = id; return true; }
+                    continue;
+                }
+                if (TRACK && h.tri >= 0 && fabsf(t - h.t) <= TIE_REL * h.t) {
+                    cand.add(h.t, h.tri);
+                    cand.add(t, id);
+                }
+                if (t < h.t || (t == h.t && id < h.tri)) {
+                    h.t = t; h.u = u; h.v = v; h.tri = id;
+                }
             }
-            bool inside = (u >= -eps_w) && (v >= -eps_w) && (u + v <= 1.0f + eps_w) && (t > 0.0f);
-            if (!inside) continue;
-            if (ANYHIT) {
-                if (t < tmax) { h.t = t; h.tri = id; return true; }
-                continue;
-            }
-            if (TRACK && h.tri >= 0 && fabsf(t - h.t) <= TIE_REL * h.t) {
-                cand.add(h.t, h.tri);
-                cand.add(t, id);
-            }
-            if (t < h.t || (t == h.t && id < h.tri)) {
-                h.t = t; h.u = u; h.v = v; h.tri = id;
+            LEAF = 0;
+            if (node < 0) {
+                LEAF = node;
+                node = sp > 0 ? stk[(--sp) * SSTRIDE] : SENT;
             }
         }
-        if (sp == 0) break;
-        node = stk[(--sp) * SSTRIDE];
+        if (node == SENT) break;
     }
     return h.tri >= 0;
 }
