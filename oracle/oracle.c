@@ -98,6 +98,31 @@ static double phase_draw(const or_render *r, int lam, const int64_t cell[3], int
     return u24(o[m & 3]);
 }
 
+/* Eq. 4: phase of hologram m (relative to hologram_offset) at the image point's position
+   (x_Q, y_Q) on the hologram plane: the sample of the periodic GRF grid, of the SLM's pitch,
+   whose cell [j - n/2, j + 1 - n/2) * pitch contains it.  Returned in turns. */
+static double grf_phase(const or_render *r, double qx, double qy, int m)
+{
+    const int64_t nx = r->grf_nx, ny = r->grf_ny;
+    const double inv_p = 1.0 / r->pitch;
+    int64_t jx = (int64_t)floor(qx * inv_p + 0.5 * (double)nx) % nx;
+    int64_t jy = (int64_t)floor(qy * inv_p + 0.5 * (double)ny) % ny;
+    if (jx < 0) jx += nx;
+    if (jy < 0) jy += ny;
+    return r->grf_phi[((int64_t)m * ny + jy) * nx + jx] / (2.0 * PI);
+}
+
+void or_grf_phases(uint64_t seed, int32_t m, int32_t nx, int32_t ny, double *xi)
+{
+    const uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int32_t iy = 0; iy < ny; iy++)
+        for (int32_t ix = 0; ix < nx; ix++) {
+            uint32_t c[4] = {(uint32_t)ix, (uint32_t)iy, (uint32_t)m, 0x47524600u}, o[4];
+            or_philox4x32_10(c, k, o);
+            xi[(int64_t)iy * nx + ix] = 2.0 * PI * u24(o[0]);
+        }
+}
+
 /* ------------------------------------------------------------------------ */
 /* binary16 -> double, from the IEEE 754 layout                              */
 /* ------------------------------------------------------------------------ */
@@ -826,6 +851,7 @@ static int sample_ill_conditioned(ctx_t *C, surf_t S, v3 wo, int v, double L)
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double A, beta, L, opl, r, cos_t, cos_p, base, sens;
+    double qx, qy;   /* Q on the hologram plane */
     v3 P;
     int vP, tri;
     int64_t cell[3];
@@ -889,6 +915,8 @@ static int coherent_sample(ctx_t *C, samp_t *out)
                 double g = sqrt(beta) * fabs(cos_t) / (rr * pdf_A * lambda);
                 out->sens = g * fmin(C->dA, sqrt(fmax(L, 0.0)) + sqrt(C->Lmax));
             }
+            out->qx = Q.x;
+            out->qy = Q.y;
             out->P = P;
             out->vP = v;
             out->tri = h.tri;
@@ -989,6 +1017,7 @@ static void pixel_field(ctx_t *C, double *ure, double *uim)
         for (int m = 0; m < K; m++) {
             double ph = 0.0;
             if (r->phase_mode == 0) ph = phase_draw(r, C->lam, S.cell, r->hologram_offset + m);
+            else if (r->phase_mode == 2) ph = grf_phase(r, S.qx, S.qy, m);
             double t = turns_r + ph;
             /* (1/(i lambda)) folded into base; multiply by -i */
             double c = cos(2.0 * PI * t), sn = sin(2.0 * PI * t);
@@ -1006,6 +1035,7 @@ static void pixel_field(ctx_t *C, double *ure, double *uim)
 int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double *rec)
 {
     const oracle_t *o = h;
+    if (r->phase_mode == 2 && (!r->grf_phi || r->grf_nx < 1 || r->grf_ny < 1)) return -1;
     ctx_t C = {o, r, lam, r->channel[lam], s, pixel, 0, 0, 1, 0.0, 0.0, 0.0};
     samp_t S;
     memset(&S, 0, sizeof S);
@@ -1020,7 +1050,10 @@ int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double
     rec[OR_REC_L] = S.L; rec[OR_REC_BETA] = S.beta; rec[OR_REC_OPL] = S.opl; rec[OR_REC_R] = S.r;
     rec[OR_REC_COS] = S.cos_t; rec[OR_REC_COSP] = S.cos_p; rec[OR_REC_VP] = S.vP;
     rec[OR_REC_PX] = S.P.x; rec[OR_REC_PY] = S.P.y; rec[OR_REC_PZ] = S.P.z; rec[OR_REC_TRI] = S.tri;
-    double ph = r->phase_mode == 0 ? phase_draw(r, lam, S.cell, r->hologram_offset) : 0.0;
+    double ph = r->phase_mode == 0 ? phase_draw(r, lam, S.cell, r->hologram_offset)
+              : r->phase_mode == 2 ? grf_phase(r, S.qx, S.qy, 0) : 0.0;
+    rec[OR_REC_QX] = S.qx;
+    rec[OR_REC_QY] = S.qy;
     double t = fmod(S.r / r->lambda[lam], 1.0) + ph;
     rec[OR_REC_RE] = S.base * sin(2.0 * PI * t);
     rec[OR_REC_IM] = -S.base * cos(2.0 * PI * t);
@@ -1077,6 +1110,7 @@ int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixel
              double *out, int64_t *flags, double *sens, int n_threads)
 {
     if (!h || !r || r->K < 1 || r->K > 64 || r->n_lambda < 1 || r->n_lambda > 3 || r->spp < 1) return -1;
+    if (r->phase_mode == 2 && (!r->grf_phi || r->grf_nx < 1 || r->grf_ny < 1)) return -1;
     for (int64_t i = 0; i < n_pixels; i++)
         if (pixels[i] < 0 || pixels[i] >= (int64_t)r->W * r->H) return -2;
     if (n_threads < 1) n_threads = 1;

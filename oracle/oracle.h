@@ -55,16 +55,20 @@ typedef struct {
     double facet_size;
     double T[16];            /* world -> hologram, row-major, rigid */
     int32_t use_cache;
+    int32_t grf_nx, grf_ny;  /* phase_mode 2: periodic GRF phase grid (pitch = the SLM pitch) */
+    const double *grf_phi;   /* [K][grf_ny][grf_nx] radians, hologram_offset + m for map m */
 } or_render;
 
 /* per-sample debug record (or_sample) */
 enum { OR_REC_L, OR_REC_BETA, OR_REC_OPL, OR_REC_R, OR_REC_COS, OR_REC_COSP, OR_REC_VP,
        OR_REC_PX, OR_REC_PY, OR_REC_PZ, OR_REC_TRI, OR_REC_FLAGS, OR_REC_RE, OR_REC_IM,
-       OR_REC_NRAYS, OR_REC_U0, OR_REC_N };
+       OR_REC_NRAYS, OR_REC_U0, OR_REC_QX, OR_REC_QY, OR_REC_N };
 
 void *or_build(const or_scene *s);
 void or_free(void *h);
-/* out: [n_lambda][K][n_pixels][2] complex128.  flags (optional): [n_lambda][n_pixels], three
+/* phase_mode: 0 hashed facet phase, 1 zero phase, 2 GRF phase maps (Eq. 4) sampled at the
+ * image point's hologram-plane position Q.
+ * out: [n_lambda][K][n_pixels][2] complex128.  flags (optional): [n_lambda][n_pixels], three
  * 16-bit sample counts: bits 0-15 samples with a ray query near a triangle edge or tie; bits
  * 16-31 samples whose incoherent part is ill-conditioned (a rounding-sized move of the image
  * point changes its radiance by more than 30x as much, relatively); bits 32-47 samples whose
@@ -88,6 +92,9 @@ int or_ggx_sample(double alpha, double F0, const double wo[3], double u0, double
                   double wi[3], double *weight, double *pdf);
 void or_frame(const double n[3], double t[3], double b[3]);
 double or_half_to_double(uint16_t h);
+/* Eq. 4: the random spectral phases xi_m(fx, fy) of GRF map m on an nx x ny frequency grid in
+ * FFT order, row-major [ny][nx]: xi = 2 pi u24(Philox4x32-10(ix, iy, m, 0x47524600; seed)). */
+void or_grf_phases(uint64_t seed, int32_t m, int32_t nx, int32_t ny, double *xi);
 
 #ifdef __cplusplus
 }

@@ -49,11 +49,12 @@ class OrRender(C.Structure):
                 ("lam", C.c_double * 3), ("channel", C.c_int32 * 3), ("spp", C.c_int32),
                 ("max_depth", C.c_int32), ("K", C.c_int32), ("hologram_offset", C.c_int32),
                 ("seed", C.c_uint64), ("phase_seed", C.c_uint64), ("phase_mode", C.c_int32),
-                ("facet_size", C.c_double), ("T", C.c_double * 16), ("use_cache", C.c_int32)]
+                ("facet_size", C.c_double), ("T", C.c_double * 16), ("use_cache", C.c_int32),
+                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("grf_phi", C.c_void_p)]
 
 
 REC_FIELDS = ["L", "beta", "opl", "r", "cos", "cosP", "vP", "Px", "Py", "Pz", "tri", "flags",
-              "re", "im", "nrays", "u0"]
+              "re", "im", "nrays", "u0", "Qx", "Qy"]
 
 
 def _load():
@@ -70,6 +71,8 @@ def _load():
             lib.or_sample.restype = C.c_int
             lib.or_sample.argtypes = [C.c_void_p, C.POINTER(OrRender), C.c_int, C.c_int64, C.c_int, C.c_void_p]
             lib.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_grf_phases.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+            lib.or_grf_phases.restype = None
             lib.or_cone_dir.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                         C.POINTER(C.c_double)]
             lib.or_closest_hit.restype = C.c_int
@@ -93,7 +96,8 @@ def _ptr(a):
     return a.ctypes.data if a is not None else None
 
 
-def _render_struct(r) -> OrRender:
+def _render_struct(r, grf=None) -> OrRender:
+    """grf: phase maps [K][ny][nx] (radians, float64) for phase_mode 2, kept alive by the caller."""
     s = OrRender()
     s.W, s.H, s.pitch = int(r.W), int(r.H), float(r.pitch)
     s.n_lambda = len(r.lambdas)
@@ -107,6 +111,10 @@ def _render_struct(r) -> OrRender:
     for i in range(16):
         s.T[i] = float(T[i])
     s.use_cache = int(r.use_cache)
+    if grf is not None:
+        assert grf.dtype == np.float64 and grf.flags.c_contiguous and grf.ndim == 3 and grf.shape[0] >= r.K
+        s.grf_ny, s.grf_nx = int(grf.shape[1]), int(grf.shape[2])
+        s.grf_phi = grf.ctypes.data
     return s
 
 
@@ -159,10 +167,11 @@ class Oracle:
         except Exception:
             pass
 
-    def trace(self, render, pixels=None, n_threads=None, with_flags=False):
+    def trace(self, render, pixels=None, n_threads=None, with_flags=False, grf=None):
         """U[lambda][m][pixel] (complex128) for the listed pixel linear indices (all by default).
         with_flags: also the per-pixel flag counts and delta-chain sensitivity bound
-        [lambda][pixel] (see or_trace), returned as (U, flags, sens)."""
+        [lambda][pixel] (see or_trace), returned as (U, flags, sens).  grf: the phase maps of
+        phase_mode 2 (``waveoptics.grf_maps``)."""
         if pixels is None:
             pixels = np.arange(render.W * render.H, dtype=np.int64)
         pixels = np.ascontiguousarray(pixels, np.int64)
@@ -171,7 +180,8 @@ class Oracle:
         out = np.zeros((nl, render.K, n, 2), np.float64)
         flags = np.zeros((nl, n), np.int64)
         sens = np.zeros((nl, n), np.float64)
-        rs = _render_struct(render)
+        grf = None if grf is None else np.ascontiguousarray(grf, np.float64)
+        rs = _render_struct(render, grf)
         nt = n_threads or os.cpu_count() or 1
         rc = self._lib.or_trace(self._h, C.byref(rs), pixels.ctypes.data, n, out.ctypes.data,
                                 flags.ctypes.data if with_flags else None,
@@ -181,13 +191,14 @@ class Oracle:
         U = out[..., 0] + 1j * out[..., 1]
         return (U, flags, sens) if with_flags else U
 
-    def trace_full(self, render, n_threads=None):
-        U = self.trace(render, None, n_threads)
+    def trace_full(self, render, n_threads=None, grf=None):
+        U = self.trace(render, None, n_threads, grf=grf)
         return U.reshape(len(render.lambdas), render.K, render.H, render.W)
 
-    def sample(self, render, lam, pixel, s):
+    def sample(self, render, lam, pixel, s, grf=None):
         rec = np.zeros(len(REC_FIELDS), np.float64)
-        rs = _render_struct(render)
+        grf = None if grf is None else np.ascontiguousarray(grf, np.float64)
+        rs = _render_struct(render, grf)
         ok = self._lib.or_sample(self._h, C.byref(rs), int(lam), int(pixel), int(s), rec.ctypes.data)
         d = dict(zip(REC_FIELDS, rec.tolist()))
         d["ok"] = bool(ok)
@@ -254,3 +265,10 @@ def frame(n):
 
 def half_to_double(h):
     return _load().or_half_to_double(int(h))
+
+
+def grf_phases(seed, m, nx, ny):
+    """Random spectral phases xi_m of GRF map m, [ny][nx] in FFT order (Eq. 4)."""
+    xi = np.zeros((ny, nx), np.float64)
+    _load().or_grf_phases(int(seed), int(m), int(nx), int(ny), xi.ctypes.data)
+    return xi

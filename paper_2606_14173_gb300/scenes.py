@@ -34,7 +34,7 @@ LAMBERT, GGX, MIRROR, DIELECTRIC, EMITTER = 0, 1, 2, 3, 4
 MATERIAL_NAMES = {LAMBERT: "lambert", GGX: "ggx", MIRROR: "mirror",
                   DIELECTRIC: "dielectric", EMITTER: "emitter"}
 
-PHASE_HASH, PHASE_ZERO = 0, 1
+PHASE_HASH, PHASE_ZERO, PHASE_GRF = 0, 1, 2
 MM = 1e-3
 UM = 1e-6
 NM = 1e-9
