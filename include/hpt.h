@@ -55,7 +55,7 @@ enum {
 
 /* material kinds (Sec. 4.2: mirror and dielectric are delta lobes, the rest non-delta) */
 enum { HPT_LAMBERT = 0, HPT_GGX = 1, HPT_MIRROR = 2, HPT_DIELECTRIC = 3, HPT_EMITTER = 4 };
-enum { HPT_PHASE_HASH = 0, HPT_PHASE_ZERO = 1 };
+enum { HPT_PHASE_HASH = 0, HPT_PHASE_ZERO = 1, HPT_PHASE_GRF = 2 };
 /* arithmetic of the coherent chain (ray origin/direction, hit distance, OPL, phase):
  * FP64 = native double; DF32 = double-float (unevaluated sum of two floats, ~48-bit mantissa) */
 enum { HPT_PREC_FP64 = 0, HPT_PREC_DF32 = 1 };
@@ -128,10 +128,16 @@ typedef struct {
  *  K             holograms from one path set (Path Reuse), 1..8; hologram_offset shifts m
  *  seed          key of the path draws; phase_seed key of the facet phases
  *  phase_mode    HPT_PHASE_HASH: phi_m uniform in [0, 2 pi) per facet cell (edge
- *                facet_size, world space) and hologram; HPT_PHASE_ZERO: phi_m = 0
+ *                facet_size, world space) and hologram; HPT_PHASE_ZERO: phi_m = 0;
+ *                HPT_PHASE_GRF: phi_m = grf_phi[m][jy][jx], the band-limited Gaussian
+ *                random field of Eq. 4 (hpt_grf_build) at the image point's hologram-plane
+ *                position Q = (x_Q, y_Q): jx = floor(x_Q / pitch + grf_nx / 2) mod grf_nx,
+ *                likewise jy (m counts from 0 for hologram hologram_offset)
  *  T             world -> hologram transform, row-major 4x4, must be rigid
  *  precision     HPT_PREC_FP64 or HPT_PREC_DF32 (coherent chain arithmetic)
- *  use_cache     read the scene's ambient cache past the first incoherent bounce          */
+ *  use_cache     read the scene's ambient cache past the first incoherent bounce
+ *  grf_phi       HPT_PHASE_GRF only: device pointer, float radians [K][grf_ny][grf_nx],
+ *                caller-owned, must stay valid until the trace completes; else NULL    */
 typedef struct {
     int32_t W, H;
     double pitch;
@@ -145,6 +151,8 @@ typedef struct {
     double T[16];
     int32_t precision;
     int32_t use_cache;
+    const float *grf_phi;
+    int32_t grf_nx, grf_ny;
 } hpt_render_desc;
 
 /* Output layout of every trace: complex64 (float re, float im) [n_lambda][K][H][W];
@@ -208,6 +216,32 @@ hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
  * do not depend on the wave size. */
 hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                         int32_t *paths_per_wave);
+
+/* ---- wave optics around the tracer: GRF phase maps and angular-spectrum propagation ---- */
+/* Eq. 4 (Sec. 4.3): for m = hologram_offset .. hologram_offset + K - 1, the band-limited
+ * Gaussian random field r_m = F^-1{ chi exp(i xi_m) } on a periodic nx x ny grid of the given
+ * pitch, chi the circular passband |f| <= sin(theta_max)/lambda = 1/(2 pitch) (frequencies
+ * kx/(nx pitch), ky/(ny pitch) in FFT order, inside when 4 (kx^2 ny^2 + ky^2 nx^2) <=
+ * nx^2 ny^2), xi_m = 2 pi u24(Philox4x32-10(kx mod nx, ky mod ny, m, 0x47524600; phase_seed)),
+ * and writes phi_m = arg r_m in radians, float [K][ny][nx], to phi_dev (caller-owned device
+ * memory, 4 K nx ny bytes).  nx, ny: powers of two, 2 .. 8192.  Runs on 'stream' (NULL: the
+ * legacy default stream); scratch is taken from the context.  The paper's own numbers for the
+ * grid are not given: the caller chooses it to cover the image points' hologram positions
+ * (the field is periodic). */
+hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t hologram_offset, int32_t K,
+                         int32_t nx, int32_t ny, double pitch, float *phi_dev, void *stream);
+
+/* Angular spectrum method (Sec. 3, "Angular Spectrum of Wave Field"; the two-stage scheme of
+ * Sec. 5): propagate each of the n_lambda * K complex64 fields [n_lambda][K][H][W] in in_dev
+ * by z metres (light travelling from the recording plane towards the SLM: z > 0) and write
+ * them to out_dev (same layout; may equal in_dev).  Each field is zero-padded to Wp x Hp,
+ * the next powers of two of at least 2W and 2H (centred at ((Wp - W)/2, (Hp - H)/2)), its
+ * spectrum multiplied by exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) (0 where the root is
+ * imaginary), transformed back and cropped to the original window.  lambdas: host array of
+ * n_lambda wavelengths (m).  Wp, Hp <= 8192.  Asynchronous on 'stream'. */
+hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, int32_t W, int32_t H,
+                             int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
+                             void *stream);
 
 /* ---- serving: continuous batching of render requests ---------------------------------- */
 /* Queue a request; the scheduler thread admits it when a slot and memory are free and runs

@@ -713,7 +713,11 @@ static hpt_status make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
     if (r->spp < 1 || r->max_depth < 1 || r->max_depth > 64) return fail(HPT_ERR_INVALID_ARG, "bad spp or max_depth");
     if (r->K < 1 || r->K > KMAX) return fail(HPT_ERR_INVALID_ARG, "K must be 1..%d", KMAX);
     if (r->hologram_offset < 0 || r->hologram_offset + r->K > (1 << 18)) return fail(HPT_ERR_INVALID_ARG, "bad hologram_offset");
-    if (r->phase_mode != HPT_PHASE_HASH && r->phase_mode != HPT_PHASE_ZERO) return fail(HPT_ERR_INVALID_ARG, "bad phase_mode");
+    if (r->phase_mode != HPT_PHASE_HASH && r->phase_mode != HPT_PHASE_ZERO && r->phase_mode != HPT_PHASE_GRF)
+        return fail(HPT_ERR_INVALID_ARG, "bad phase_mode");
+    if (r->phase_mode == HPT_PHASE_GRF && (!r->grf_phi || r->grf_nx < 1 || r->grf_ny < 1 || r->grf_nx > (1 << 16) ||
+                                           r->grf_ny > (1 << 16)))
+        return fail(HPT_ERR_INVALID_ARG, "phase_mode GRF needs grf_phi and 1 <= grf_nx, grf_ny <= 65536");
     if (r->precision != HPT_PREC_FP64 && r->precision != HPT_PREC_DF32) return fail(HPT_ERR_INVALID_ARG, "bad precision");
     if (!(r->facet_size > 0.0) || !std::isfinite(r->facet_size)) return fail(HPT_ERR_INVALID_ARG, "bad facet_size");
     for (int i = 0; i < 16; ++i)
@@ -749,6 +753,9 @@ static hpt_status make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
     J.K = r->K;
     J.hologram_offset = r->hologram_offset;
     J.phase_mode = r->phase_mode;
+    J.grf = r->phase_mode == HPT_PHASE_GRF ? r->grf_phi : nullptr;
+    J.grf_nx = r->phase_mode == HPT_PHASE_GRF ? r->grf_nx : 0;
+    J.grf_ny = r->phase_mode == HPT_PHASE_GRF ? r->grf_ny : 0;
     J.use_cache = r->use_cache ? 1 : 0;
     J.n_tiles_x = (r->W + TILE_W - 1) / TILE_W;
     J.n_tiles = J.n_tiles_x * ((r->H + TILE_H - 1) / TILE_H);
@@ -774,6 +781,7 @@ static hpt_status make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
     }
     J.pitch = make_rc(r->pitch);
     J.inv_facet = make_rc(1.0 / r->facet_size);
+    J.inv_pitch = make_rc(1.0 / r->pitch);
     bool ident = true;
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) {
@@ -1493,4 +1501,9 @@ int internal_grid(const hpt_ctx *ctx, int prec, int which)
     return which == 0 ? ctx->grid_trace[prec] : ctx->grid_shade[prec];
 }
 hpt_status internal_fail(hpt_status st, const char *msg) { return fail(st, "%s", msg); }
+hpt_status internal_check(hpt_ctx *ctx)
+{
+    g_err.clear();
+    return check_ctx(ctx);
+}
 }  // namespace hpt

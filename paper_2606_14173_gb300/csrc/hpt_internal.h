@@ -89,6 +89,9 @@ struct DevJob {
     RC R[9];                    // rotation of T (world -> hologram), row-major
     RC t[3];                    // translation of T
     const float4 *sincos_tab;   // cos/sin(2 pi k / 256) as (hi, lo) float pairs, 256 entries
+    const float *grf;           // phase mode 2: [K][grf_ny][grf_nx] radians
+    int grf_nx, grf_ny;
+    RC inv_pitch;
 };
 
 struct JobTable {

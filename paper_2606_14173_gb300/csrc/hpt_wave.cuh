@@ -493,9 +493,26 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
                     const float cosP = fabsf(dot3(dl, ng));
                     const R ih = RO::rc(J.inv_facet);
                     pb.fturn[p] = RO::frac_f(opl * RO::rc(J.inv_lambda[id.lam]));
-                    pb.cx[p] = RO::floor_i(P.x * ih);
-                    pb.cy[p] = RO::floor_i(P.y * ih);
-                    pb.cz[p] = RO::floor_i(P.z * ih);
+                    if (J.phase_mode == 2) {
+                        // Eq. 4: the GRF sample under Q = x + d_OPL dh on the hologram plane
+                        // (rigid T), dh the sampled hologram-space direction, redrawn here
+                        const float4 u0 = path_draw(J, id.pix, (unsigned)id.s, 0u, 0u, (unsigned)id.lam);
+                        const R s1 = RO::mulf(RO::rc(J.h_cone[id.lam]), u0.x);
+                        const R sn = RO::sqrt_(s1 * (RO::f(2.0f) - s1));
+                        R sp, cp;
+                        RO::sincos2pi(u0.y, J.sincos_tab, sp, cp);
+                        const R xq = RO::mulf(RO::rc(J.pitch), (float)id.px + 0.5f - 0.5f * (float)J.W) + opl * (sn * cp);
+                        const R yq = RO::mulf(RO::rc(J.pitch), (float)id.py + 0.5f - 0.5f * (float)J.H) + opl * (sn * sp);
+                        int jx = RO::floor_i(RO::addf(xq * RO::rc(J.inv_pitch), 0.5f * (float)J.grf_nx)) % J.grf_nx;
+                        int jy = RO::floor_i(RO::addf(yq * RO::rc(J.inv_pitch), 0.5f * (float)J.grf_ny)) % J.grf_ny;
+                        pb.cx[p] = jx < 0 ? jx + J.grf_nx : jx;
+                        pb.cy[p] = jy < 0 ? jy + J.grf_ny : jy;
+                        pb.cz[p] = 0;
+                    } else {
+                        pb.cx[p] = RO::floor_i(P.x * ih);
+                        pb.cy[p] = RO::floor_i(P.y * ih);
+                        pb.cz[p] = RO::floor_i(P.z * ih);
+                    }
                     pb.basep[p] = pb.cost[p] * RO::to_f(opl) / (J.pdf_w[id.lam] * cosP * J.lambda_f[id.lam]);
                     st.L = 0.0f;
                     st.beta = 1.0f;
@@ -711,6 +728,9 @@ __global__ void __launch_bounds__(ACCUM_BLOCK) k_accum(const JobTable *__restric
                                     J.pseed_hi);
                     const unsigned w = (m & 3) == 0 ? ph.x : ((m & 3) == 1 ? ph.y : ((m & 3) == 2 ? ph.z : ph.w));
                     u = u24(w);
+                } else if (J.phase_mode == 2) {
+                    // Eq. 4: phi_m sampled from the hologram's GRF map at the cell of Q
+                    u = __ldg(J.grf + ((size_t)j * J.grf_ny + c1) * J.grf_nx + c0) * 0.159154943f;
                 }
                 float sn, cs;
                 sincospif(2.0f * (ft + u), &sn, &cs);

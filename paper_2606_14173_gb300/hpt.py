@@ -24,7 +24,8 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 # exported symbols, as declared in include/hpt.h
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
-           "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed"]
+           "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
+           "hpt_asm_propagate"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -60,7 +61,8 @@ class RenderDesc(C.Structure):
                 ("lam", C.c_double * 3), ("channel", C.c_int32 * 3), ("spp", C.c_int32), ("max_depth", C.c_int32),
                 ("K", C.c_int32), ("hologram_offset", C.c_int32), ("seed", C.c_uint64), ("phase_seed", C.c_uint64),
                 ("phase_mode", C.c_int32), ("facet_size", C.c_double), ("T", C.c_double * 16),
-                ("precision", C.c_int32), ("use_cache", C.c_int32)]
+                ("precision", C.c_int32), ("use_cache", C.c_int32), ("grf_phi", C.c_void_p),
+                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32)]
 
 
 _lib = None
@@ -86,6 +88,9 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_grf_build.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, vp]
+    lib.hpt_asm_propagate.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                      C.c_double, C.c_double, vp]
     lib.hpt_trace_timed.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_float),
                                     C.POINTER(C.c_uint32)]
     lib.hpt_submit.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
@@ -122,6 +127,13 @@ def render_desc(r, precision=PREC_DF32) -> RenderDesc:
         d.T[i] = float(T[i])
     d.precision = int(precision)
     d.use_cache = int(r.use_cache)
+    g = getattr(r, "grf", None)
+    if g is not None:
+        if not (g.is_cuda and g.dtype.is_floating_point and g.element_size() == 4 and g.is_contiguous()
+                and g.dim() == 3 and g.shape[0] >= r.K):
+            raise ValueError("grf must be a contiguous float32 CUDA tensor [>= K][ny][nx]")
+        d.grf_phi = g.data_ptr()
+        d.grf_ny, d.grf_nx = int(g.shape[1]), int(g.shape[2])
     return d
 
 
@@ -242,6 +254,29 @@ class Context:
         n = (C.c_uint32 * len(KERNEL_NAMES))()
         _check(self.lib.hpt_trace_timed(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, ms, n))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def grf_build(self, phase_seed: int, K: int, nx: int, ny: int, pitch: float, hologram_offset: int = 0,
+                  stream=None):
+        """Eq. 4 phase maps [K][ny][nx] (float32 radians) as a new CUDA tensor."""
+        import torch
+        phi = torch.empty((K, ny, nx), dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(self.lib.hpt_grf_build(self.h, C.c_uint64(phase_seed), int(hologram_offset), int(K), int(nx), int(ny),
+                                      float(pitch), C.c_void_p(phi.data_ptr()), _stream_ptr(stream)))
+        return phi
+
+    def asm_propagate(self, U, lambdas, pitch: float, z: float, out=None, stream=None):
+        """Angular-spectrum propagation by z of fields U [n_lambda][K][H][W] (complex64, CUDA)."""
+        if not (U.is_cuda and U.dtype.is_complex and U.element_size() == 8 and U.is_contiguous() and U.dim() == 4):
+            raise ValueError("U must be a contiguous complex64 CUDA tensor [n_lambda][K][H][W]")
+        nl, K, H, W = (int(x) for x in U.shape)
+        if len(lambdas) != nl:
+            raise ValueError("one wavelength per field group")
+        if out is None:
+            out = U.new_empty(U.shape)
+        lam = (C.c_double * nl)(*[float(x) for x in lambdas])
+        _check(self.lib.hpt_asm_propagate(self.h, C.c_void_p(U.data_ptr()), C.c_void_p(out.data_ptr()), W, H, nl, K,
+                                          lam, float(pitch), float(z), _stream_ptr(stream)))
+        return out
 
     def autotune(self, sid: int, r, precision=PREC_DF32) -> int:
         """Pick the wave size by timing a band of this render; returns paths per wave."""

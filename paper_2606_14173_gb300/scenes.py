@@ -106,6 +106,7 @@ class Render:
     facet_size: float = 16 * UM        # edge of the cubic facet cells of the hash phase
     T: np.ndarray = field(default_factory=lambda: np.eye(4))  # world -> hologram
     use_cache: int = 0
+    grf: object = None                 # phase mode 2: device phase maps [K][ny][nx] (float32 radians)
 
     @property
     def n_lambda(self) -> int:

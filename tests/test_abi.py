@@ -8,6 +8,7 @@ import tempfile
 import pytest
 
 from paper_2606_14173_gb300 import hpt
+from paper_2606_14173_gb300.scenes import PHASE_GRF as S_PHASE_GRF
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "hpt.h")
@@ -44,6 +45,8 @@ int main(void) {
          offsetof(hpt_scene_desc, cache_E), offsetof(hpt_render_desc, seed), offsetof(hpt_render_desc, T));
   printf("%zu %zu\n", offsetof(hpt_render_desc, precision), offsetof(hpt_render_desc, use_cache));
   printf("%d %d %d %d\n", HPT_NCOUNTERS, HPT_NKERNELS, HPT_K_TRACE, HPT_K_ACCUM);
+  printf("%zu %zu %zu %d\n", offsetof(hpt_render_desc, grf_phi), offsetof(hpt_render_desc, grf_nx),
+         offsetof(hpt_render_desc, grf_ny), HPT_PHASE_GRF);
   return 0;
 }
 '''
@@ -58,7 +61,8 @@ int main(void) {
            hpt.SceneDesc.tex_floats.offset, hpt.SceneDesc.cache_res.offset, hpt.SceneDesc.cache_E.offset,
            hpt.RenderDesc.seed.offset, hpt.RenderDesc.T.offset, hpt.RenderDesc.precision.offset,
            hpt.RenderDesc.use_cache.offset, hpt.NCOUNTERS, len(hpt.KERNEL_NAMES),
-           hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum")]
+           hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum"),
+           hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF]
     assert [int(x) for x in out] == got
 
 
