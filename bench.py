@@ -13,6 +13,7 @@ batched form (double-float coherent arithmetic, all wavelengths and holograms in
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -31,6 +32,15 @@ UNIT = "path samples/s"
 # FP32 ALU peak of a GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA
 # x 2.07 GHz (maximum SM clock).
 SM_COUNT, FP32_LANES, SM_MHZ_MAX = 152, 128, 2070.0
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
 ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 # algorithmic FP32 work per counted event (see the design notes): two child-box slab tests per
 # node visit are counted as two box tests
@@ -64,6 +74,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-counters", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-optics", action="store_true")
     p.add_argument("--workload", default="cfg2", choices=list(WORKLOADS),
                    help="cfg2 = the headline workload; the others are smaller cases of the same kernels for profiling")
     return p.parse_args()
@@ -209,6 +220,51 @@ def serve(ctx, hpt, S, requests, rate, seed):
             "span_s": float(span)}
 
 
+def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
+    """The wave-optics steps around the tracer on the headline output: the K GRF phase maps of
+    Eq. 4 (4096 x 2048 grid of the SLM pitch), the angular-spectrum propagation of all
+    n_lambda x K fields over 80 mm (the two-stage scheme; 4096 x 4096 padded), and a traced
+    frame in GRF phase mode.  Device time from CUDA events on the bench stream."""
+    def timed_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    nx, ny = 4096, 2048
+    grf = {}
+    grf_ms = timed_ms(lambda: grf.__setitem__("phi", ctx.grf_build(r.phase_seed, r.K, nx, ny, r.pitch, stream=stream)))
+    res = torch.empty_like(out)
+    asm_ms = timed_ms(lambda: ctx.asm_propagate(out, r.lambdas, r.pitch, 80e-3, out=res, stream=stream))
+    Wp = Hp = 4096
+    n_fields = len(r.lambdas) * r.K
+    # algorithmic bytes per field: two 2-D FFTs of four row passes' worth of read + write each
+    # (a 2-D FFT needs every element read and written once per dimension and direction), the
+    # transfer function read once, the field read and written once
+    alg = n_fields * (2 * 2 * 2 * 8 * Wp * Hp + 8 * Wp * Hp + 2 * 8 * r.W * r.H)
+    achieved = alg / (asm_ms / 1e3) / 1e9
+    rg = dataclasses.replace(r, phase_mode=2, grf=grf["phi"])
+    grf_trace_ms = timed_ms(lambda: ctx.trace(sid, rg, out, precision=hpt.PREC_DF32, stream=stream))
+    return {
+        "grf_maps": {"K": r.K, "grid": [nx, ny], "ms": grf_ms, "maps_per_s": r.K / (grf_ms / 1e3)},
+        "asm": {"fields": n_fields, "field": [r.W, r.H], "padded": [Wp, Hp], "z_m": 80e-3, "ms": asm_ms,
+                "fields_per_s": n_fields / (asm_ms / 1e3),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                             "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                             "alg_bytes_per_field": alg / n_fields,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}},
+        "grf_phase_trace": {"ms_per_frame": grf_trace_ms,
+                            "path_samples_per_s": r.path_samples() / (grf_trace_ms / 1e3)},
+        "workload": "headline output (1920x1080, RGB, K = 8): GRF maps 4096x2048, ASM of 24 fields over 80 mm, "
+                    "one frame traced with GRF phases",
+    }
+
+
 def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
     """(a) headline requests (1080p RGB 64 spp depth 4 K=8) at 2 req/s, near the device's capacity;
     (b) a mixed request stream at 40 req/s following the serving recipe (poses, focal depths,
@@ -316,6 +372,7 @@ def main():
             clk.start()
             clk.wait_ready()
         for _ in range(w):
+            flush.zero_()        # also loads the flush kernel before the timed region
             step()
         ctx.sync()
         barrier(world)
@@ -339,7 +396,11 @@ def main():
         ctx.sync()
         total_ms = t0.elapsed_time(t1)
         launch_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(k)]
+        gaps = [t0.elapsed_time(ev[0])] + [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(k - 1)]
+        gaps_ms.append(gaps + [ev[2 * k - 1].elapsed_time(t1)])
         return allreduce_max(total_ms, world), launch_ms, clocks
+
+    gaps_ms = []
 
     total_ms, launch_ms, clocks = timed(step_mixed, args.steps, args.warmup, sample_clocks=True)
     value = world * samples_per_step * args.steps / (total_ms / 1e3)
@@ -398,6 +459,11 @@ def main():
                 "per_sample": {k: v / ns for k, v in cnt.items() if k != "samples"},
                 "flops_per_sample": flops / ns}
 
+    optics = None
+    if not args.no_optics and rank == 0:
+        optics = run_optics(ctx, hpt, torch, r, out, sid, stream)
+        ctx.sync()
+
     serving = None
     if not args.no_serving and args.workload == "cfg2":
         sid0 = ctx.upload_scene(S.config0_scene())
@@ -421,8 +487,9 @@ def main():
                            "l2": "flushed between steps (256 MiB write)"},
                 "holograms_per_s": holo_per_s, "plain_fp64": plain, "launch_ms": launch_ms,
                 "idle_ms_per_step": (total_ms - sum(launch_ms)) / args.steps,
+                "gaps_ms": [round(g, 3) for g in gaps_ms[0]],
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * sum(n for _, n in kt.values()),
-                "graph_launches": args.steps, "roofline": roofline, "serving": serving,
+                "graph_launches": args.steps, "roofline": roofline, "optics": optics, "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
