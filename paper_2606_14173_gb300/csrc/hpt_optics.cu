@@ -2,8 +2,9 @@
 // (hpt_grf_build) and the angular spectrum method of the two-stage scheme (hpt_asm_propagate).
 //
 // Both rest on one 2-D FFT of power-of-two sizes: every row transformed in shared memory by
-// one block (radix-2 decimation in time, bit-reversed load), a tiled transpose, the rows
-// again, and the transpose back.  The data are complex64; the twiddle factors are rounded
+// one block (Stockham autosort, radix 4 with one radix-2 step for odd powers of two, two
+// shared buffers so that the global loads and stores stay in natural order), a tiled
+// transpose, the rows again, and the transpose back.  The data are complex64; the twiddle factors are rounded
 // from double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
 // ~1e5 turns, is formed in double before its fraction is taken.
 #include <algorithm>
@@ -25,8 +26,8 @@ using namespace hpt;
 
 namespace {
 
-constexpr int FFT_MAX_LOG = 13;          // 8192 points: 64 KB of shared memory per row
-constexpr int FFT_THREADS = 512;
+constexpr int FFT_MAX_LOG = 13;          // 8192 points: 2 x 64 KB of shared memory per row
+constexpr int FFT_THREADS = 256;
 constexpr unsigned GRF_TAG = 0x47524600u;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -34,18 +35,68 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// tw[k] = exp(-2 pi i k / n), k < n / 2
+// tw[k] = exp(-2 pi i k / n), k < n
 __global__ void k_twiddles(float2 *tw, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n / 2) return;
+    if (k >= n) return;
     double s, c;
     sincospi(-2.0 * (double)k / (double)n, &s, &c);
     tw[k] = make_float2((float)c, (float)s);
 }
 
-// In-place FFT of 'rows' consecutive rows of n = 2^logn points.  sign = -1: forward
-// (exp(-2 pi i k j / n)), +1: inverse without the 1/n; the result is multiplied by 'scale'.
+// FFT of one row of n = 2^logn points held in shared memory x, with y as the second Stockham
+// buffer; sign = -1: forward (exp(-2 pi i k j / n)), +1: inverse without the 1/n.  Returns the
+// buffer that holds the result.  Stockham stages: with Ns the length of the sub-transforms
+// already done and R the radix, element j of the stage reads x[j + r n/R] (r < R), multiplies
+// it by exp(sign 2 pi i r (j mod Ns) / (Ns R)), takes the R-point DFT and writes it to
+// y[(j / Ns) Ns R + j mod Ns + r Ns].  Radix 4, with one radix-2 step first for odd logn.
+// The caller synchronises before (x filled) and the function ends with a barrier.
+__device__ float2 *fft_smem(float2 *x, float2 *y, int logn, float sign, const float2 *__restrict__ tw)
+{
+    const int n = 1 << logn;
+    int Ns = 1;
+    if (logn & 1) {
+        for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
+            const float2 a = x[j], b = x[j + n / 2];
+            y[2 * j] = make_float2(a.x + b.x, a.y + b.y);
+            y[2 * j + 1] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        __syncthreads();
+        float2 *t = x; x = y; y = t;
+        Ns = 2;
+    }
+    for (; Ns < n; Ns *= 4) {
+        const int q = n / 4, tws = n / (Ns * 4);
+        for (int j = threadIdx.x; j < q; j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            float2 v0 = x[j], v1 = x[j + q], v2 = x[j + 2 * q], v3 = x[j + 3 * q];
+            if (Ns > 1) {
+                float2 w1 = __ldg(tw + k * tws), w2 = __ldg(tw + 2 * k * tws), w3 = __ldg(tw + 3 * k * tws);
+                w1.y *= -sign;
+                w2.y *= -sign;
+                w3.y *= -sign;
+                v1 = cmul(v1, w1);
+                v2 = cmul(v2, w2);
+                v3 = cmul(v3, w3);
+            }
+            // 4-point DFT; forward uses -i, inverse +i
+            const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+            const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+            const float2 id13 = make_float2(-sign * d13.y, sign * d13.x);   // sign * i * d13
+            const int o = (j - k) * 4 + k;
+            y[o] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            y[o + Ns] = make_float2(d02.x + id13.x, d02.y + id13.y);
+            y[o + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            y[o + 3 * Ns] = make_float2(d02.x - id13.x, d02.y - id13.y);
+        }
+        __syncthreads();
+        float2 *t = x; x = y; y = t;
+    }
+    return x;
+}
+
+// In-place FFT of 'rows' consecutive rows of n = 2^logn points, times 'scale'.
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_rows(float2 *data, int logn, int rows, float sign,
                                                           const float2 *__restrict__ tw, float scale)
 {
@@ -53,25 +104,81 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_rows(float2 *data, int logn
     const int n = 1 << logn;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         float2 *d = data + (size_t)row * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[__brev((unsigned)i) >> (32 - logn)] = d[i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
         __syncthreads();
-        for (int s = 1; s <= logn; ++s) {
-            const int half = 1 << (s - 1), tstride = n >> s;
-            for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
-                const int pos = j & (half - 1);
-                const int i0 = ((j >> (s - 1)) << s) + pos, i1 = i0 + half;
-                float2 w = __ldg(tw + pos * tstride);
-                w.y *= -sign;
-                const float2 a = sm[i0], t = cmul(w, sm[i1]);
-                sm[i0] = make_float2(a.x + t.x, a.y + t.y);
-                sm[i1] = make_float2(a.x - t.x, a.y - t.y);
-            }
-            __syncthreads();
-        }
+        const float2 *r = fft_smem(sm, sm + n, logn, sign, tw);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const float2 v = sm[i];
+            const float2 v = r[i];
             d[i] = make_float2(v.x * scale, v.y * scale);
         }
+        __syncthreads();
+    }
+}
+
+// ASM pass 1: forward FFT of the rows of the zero-padded field.  Row r of the padded grid holds
+// in[r - oy][c - ox] for the window, 0 elsewhere; rows outside the window transform to 0.
+__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_in(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                             int logn, int rows, int W, int H, int ox, int oy,
+                                                             const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    const int n = 1 << logn;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        float2 *d = out + (size_t)row * n;
+        const int y = row - oy;
+        if (y < 0 || y >= H) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = make_float2(0.0f, 0.0f);
+            continue;
+        }
+        const float2 *src = in + (size_t)y * W;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int x = i - ox;
+            sm[i] = (x >= 0 && x < W) ? src[x] : make_float2(0.0f, 0.0f);
+        }
+        __syncthreads();
+        const float2 *r = fft_smem(sm, sm + n, logn, -1.0f, tw);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = r[i];
+        __syncthreads();
+    }
+}
+
+// ASM pass 2, on the transposed spectrum (one row per spatial frequency fx): forward FFT of the
+// row, multiplication by the transfer function's row (scale folded in), inverse FFT.
+__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_conv(float2 *data, int logn, int rows,
+                                                               const float2 *__restrict__ Ht,
+                                                               const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    const int n = 1 << logn;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        float2 *d = data + (size_t)row * n;
+        const float2 *h = Ht + (size_t)row * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
+        __syncthreads();
+        float2 *r = fft_smem(sm, sm + n, logn, -1.0f, tw);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = cmul(r[i], __ldg(h + i));
+        __syncthreads();
+        float2 *other = r == sm ? sm + n : sm;
+        const float2 *q = fft_smem(r, other, logn, +1.0f, tw);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q[i];
+        __syncthreads();
+    }
+}
+
+// ASM pass 3: inverse FFT of the rows that hold the window, cropped into the output field.
+__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_out(const float2 *__restrict__ data, float2 *__restrict__ out,
+                                                              int logn, int W, int H, int ox, int oy,
+                                                              const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    const int n = 1 << logn;
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const float2 *d = data + (size_t)(y + oy) * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
+        __syncthreads();
+        const float2 *r = fft_smem(sm, sm + n, logn, +1.0f, tw);
+        float2 *dst = out + (size_t)y * W;
+        for (int x = threadIdx.x; x < W; x += blockDim.x) dst[x] = r[x + ox];
         __syncthreads();
     }
 }
@@ -119,13 +226,14 @@ __global__ void k_arg(const float2 *__restrict__ r, float *__restrict__ phi, siz
     }
 }
 
-// exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) on the padded grid (FFT order), times 'scale'
+// exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) on the padded grid (FFT order), times 'scale',
+// stored transposed: Ht[ix][iy]
 __global__ void k_transfer(float2 *Hf, int Wp, int Hp, double pitch, double lambda, double z, float scale)
 {
     const size_t n = (size_t)Wp * Hp;
     const double il2 = 1.0 / (lambda * lambda);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % Wp), iy = (int)(i / Wp);
+        const int iy = (int)(i % Hp), ix = (int)(i / Hp);
         const double fx = (double)(ix < Wp / 2 ? ix : ix - Wp) / (Wp * pitch);
         const double fy = (double)(iy < Hp / 2 ? iy : iy - Hp) / (Hp * pitch);
         const double a = il2 - fx * fx - fy * fy;
@@ -138,30 +246,6 @@ __global__ void k_transfer(float2 *Hf, int Wp, int Hp, double pitch, double lamb
             v = make_float2(c * scale, s * scale);
         }
         Hf[i] = v;
-    }
-}
-
-__global__ void k_pad(const float2 *__restrict__ in, float2 *__restrict__ P, int W, int H, int Wp, int Hp, int ox, int oy)
-{
-    const size_t n = (size_t)Wp * Hp;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % Wp) - ox, y = (int)(i / Wp) - oy;
-        P[i] = (x >= 0 && x < W && y >= 0 && y < H) ? in[(size_t)y * W + x] : make_float2(0.0f, 0.0f);
-    }
-}
-
-__global__ void k_mul(float2 *__restrict__ P, const float2 *__restrict__ Hf, size_t n)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        P[i] = cmul(P[i], Hf[i]);
-}
-
-__global__ void k_crop(const float2 *__restrict__ P, float2 *__restrict__ out, int W, int H, int Wp, int ox, int oy)
-{
-    const size_t n = (size_t)W * H;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % W), y = (int)(i / W);
-        out[i] = P[(size_t)(y + oy) * Wp + x + ox];
     }
 }
 
@@ -185,10 +269,10 @@ cudaError_t fft2d(float2 *A, float2 *B, int nx, int ny, const float2 *twx, const
 {
     const int lx = ilog2(nx), ly = ilog2(ny);
     const dim3 tb(32, 8);
-    k_fft_rows<<<std::min(ny, 152 * 8), std::min(FFT_THREADS, std::max(32, nx / 2)), sizeof(float2) * nx, s>>>(
+    k_fft_rows<<<std::min(ny, 152 * 8), std::min(FFT_THREADS, std::max(32, nx / 4)), 2 * sizeof(float2) * nx, s>>>(
         A, lx, ny, sign, twx, 1.0f);
     k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
-    k_fft_rows<<<std::min(nx, 152 * 8), std::min(FFT_THREADS, std::max(32, ny / 2)), sizeof(float2) * ny, s>>>(
+    k_fft_rows<<<std::min(nx, 152 * 8), std::min(FFT_THREADS, std::max(32, ny / 4)), 2 * sizeof(float2) * ny, s>>>(
         B, ly, nx, sign, twy, scale);
     k_transpose<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, A, ny, nx);
     return cudaGetLastError();
@@ -198,8 +282,11 @@ cudaError_t fft_setup()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(float2) << FFT_MAX_LOG);
+    const int smem = (int)(2 * sizeof(float2)) << FFT_MAX_LOG;
+    cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_in, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_out, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -231,12 +318,12 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny;
     char *buf = nullptr;
-    const size_t bytes = 2 * n * sizeof(float2) + (size_t)(nx / 2 + ny / 2) * sizeof(float2);
+    const size_t bytes = 2 * n * sizeof(float2) + (size_t)(nx + ny) * sizeof(float2);
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
-    float2 *A = (float2 *)buf, *B = A + n, *twx = B + n, *twy = twx + nx / 2;
+    float2 *A = (float2 *)buf, *B = A + n, *twx = B + n, *twy = twx + nx;
     cudaError_t e = cudaSuccess;
-    k_twiddles<<<(nx / 2 + 255) / 256, 256, 0, s>>>(twx, nx);
-    k_twiddles<<<(ny / 2 + 255) / 256, 256, 0, s>>>(twy, ny);
+    k_twiddles<<<(nx + 255) / 256, 256, 0, s>>>(twx, nx);
+    k_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(twy, ny);
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
         k_grf_spectrum<<<grid_for(n), 256, 0, s>>>(A, nx, ny, (unsigned)(hologram_offset + k), (unsigned)phase_seed,
                                                    (unsigned)(phase_seed >> 32));
@@ -273,27 +360,32 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     OPT_TRY(fft_setup());
     cudaStream_t s = (cudaStream_t)stream;
     const size_t np = (size_t)Wp * Hp;
-    const size_t bytes = (2 + (size_t)n_lambda) * np * sizeof(float2) + (size_t)(Wp / 2 + Hp / 2) * sizeof(float2);
+    const size_t bytes = (2 + (size_t)n_lambda) * np * sizeof(float2) + (size_t)(Wp + Hp) * sizeof(float2);
     char *buf = nullptr;
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
-    float2 *A = (float2 *)buf, *B = A + np, *Hf = B + np, *twx = Hf + (size_t)n_lambda * np, *twy = twx + Wp / 2;
+    float2 *A = (float2 *)buf, *B = A + np, *Hf = B + np, *twx = Hf + (size_t)n_lambda * np, *twy = twx + Wp;
     const int ox = (Wp - W) / 2, oy = (Hp - H) / 2;
     cudaError_t e = cudaSuccess;
-    k_twiddles<<<(Wp / 2 + 255) / 256, 256, 0, s>>>(twx, Wp);
-    k_twiddles<<<(Hp / 2 + 255) / 256, 256, 0, s>>>(twy, Hp);
+    k_twiddles<<<(Wp + 255) / 256, 256, 0, s>>>(twx, Wp);
+    k_twiddles<<<(Hp + 255) / 256, 256, 0, s>>>(twy, Hp);
     for (int l = 0; l < n_lambda; ++l)
         k_transfer<<<grid_for(np), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, pitch, lambdas[l], z, 1.0f / (float)np);
     const float2 *in = (const float2 *)in_dev;
     float2 *out = (float2 *)out_dev;
+    const int lx = ilog2(Wp), ly = ilog2(Hp);
+    const dim3 tb(32, 8);
     for (int f = 0; f < n_lambda * K && e == cudaSuccess; ++f) {
         const size_t fo = (size_t)f * W * H;
-        k_pad<<<grid_for(np), 256, 0, s>>>(in + fo, A, W, H, Wp, Hp, ox, oy);
-        e = fft2d(A, B, Wp, Hp, twx, twy, -1.0f, 1.0f, s);
-        if (e != cudaSuccess) break;
-        k_mul<<<grid_for(np), 256, 0, s>>>(A, Hf + (size_t)(f / K) * np, np);
-        e = fft2d(A, B, Wp, Hp, twx, twy, +1.0f, 1.0f, s);
-        if (e != cudaSuccess) break;
-        k_crop<<<grid_for((size_t)W * H), 256, 0, s>>>(A, out + fo, W, H, Wp, ox, oy);
+        // rows of the padded field -> transpose -> per-frequency rows: FFT, transfer, inverse
+        // FFT -> transpose -> inverse FFT of the window's rows, cropped
+        k_asm_rows_in<<<std::min(Hp, 152 * 8), std::min(FFT_THREADS, std::max(32, Wp / 4)), 2 * sizeof(float2) * Wp, s>>>(
+            in + fo, A, lx, Hp, W, H, ox, oy, twx);
+        k_transpose<<<dim3((Wp + 31) / 32, (Hp + 31) / 32), tb, 0, s>>>(A, B, Wp, Hp);
+        k_asm_rows_conv<<<std::min(Wp, 152 * 8), std::min(FFT_THREADS, std::max(32, Hp / 4)), 2 * sizeof(float2) * Hp, s>>>(
+            B, ly, Wp, Hf + (size_t)(f / K) * np, twy);
+        k_transpose<<<dim3((Hp + 31) / 32, (Wp + 31) / 32), tb, 0, s>>>(B, A, Hp, Wp);
+        k_asm_rows_out<<<std::min(H, 152 * 8), std::min(FFT_THREADS, std::max(32, Wp / 4)), 2 * sizeof(float2) * Wp, s>>>(
+            A, out + fo, lx, W, H, ox, oy, twx);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(buf, s);
