@@ -1125,3 +1125,81 @@ int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixel
     pthread_mutex_destroy(&J.mu);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ambient cache construction (see oracle.h)                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const oracle_t *o;
+    const or_bake_desc *b;
+    or_render r;
+    const int64_t *cells;
+    int64_t n;
+    double *E;
+    int64_t next;
+    pthread_mutex_t mu;
+} bake_job_t;
+
+static void bake_cell(bake_job_t *J, int64_t cell, double E[3])
+{
+    const or_bake_desc *b = J->b;
+    const int64_t R = b->res;
+    const int64_t ix = cell % R, iy = (cell / R) % R, iz = cell / (R * R);
+    const int64_t idx[3] = {ix, iy, iz};
+    double xc[3];
+    for (int k = 0; k < 3; k++) xc[k] = b->bmin[k] + ((double)idx[k] + 0.5) * (b->bmax[k] - b->bmin[k]) / (double)R;
+    const v3 x = mk(xc[0], xc[1], xc[2]);
+    const int64_t pix = (iy + R * iz) * R + ix;
+    for (int c = 0; c < 3; c++) {
+        double acc = 0.0;
+        for (int s = 0; s < b->spp; s++) {
+            double u[4];
+            path_draw(&J->r, c, pix, s, 0, 0, u);
+            const double ct = 1.0 - 2.0 * u[0], st = 2.0 * sqrt(u[0] * (1.0 - u[0]));
+            const v3 d = mk(st * cos(2.0 * PI * u[1]), st * sin(2.0 * PI * u[1]), ct);
+            hit_t h;
+            if (!closest(J->o, x, d, 0.0, INFINITY, -1, 0, &h)) continue;
+            surf_t S = surface(J->o, h.tri, add(x, scl(d, h.t)), h.b1, h.b2);
+            ctx_t C = {J->o, &J->r, c, c, s, pix, 0, 0, 0, 0.0, 0.0, 0.0};
+            acc += radiance(&C, S, scl(d, -1.0), 1);
+        }
+        E[c] = PI * acc / (double)b->spp;
+    }
+}
+
+static void *bake_worker(void *arg)
+{
+    bake_job_t *J = arg;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t w = J->next;
+        J->next += 8;
+        pthread_mutex_unlock(&J->mu);
+        if (w >= J->n) break;
+        int64_t end = w + 8 < J->n ? w + 8 : J->n;
+        for (int64_t i = w; i < end; i++) bake_cell(J, J->cells[i], J->E + 3 * i);
+    }
+    return NULL;
+}
+
+int or_bake(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, int n_threads)
+{
+    if (!h || !b || b->res < 1 || b->spp < 1 || b->max_depth < 1) return -1;
+    for (int64_t i = 0; i < n_cells; i++)
+        if (cells[i] < 0 || cells[i] >= (int64_t)b->res * b->res * b->res) return -2;
+    bake_job_t J;
+    memset(&J, 0, sizeof J);
+    J.o = h; J.b = b; J.cells = cells; J.n = n_cells; J.E = E;
+    J.r.W = b->res; J.r.H = b->res * b->res; J.r.n_lambda = 3;
+    for (int c = 0; c < 3; c++) J.r.channel[c] = c;
+    J.r.spp = b->spp; J.r.max_depth = b->max_depth; J.r.K = 1; J.r.seed = b->seed;
+    J.r.phase_mode = 1; J.r.use_cache = 0;
+    pthread_mutex_init(&J.mu, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, bake_worker, &J);
+    for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&J.mu);
+    return 0;
+}

@@ -81,6 +81,24 @@ int or_trace(void *h, const or_render *r, const int64_t *pixels, int64_t n_pixel
              double *out, int64_t *flags, double *sens, int n_threads);
 int or_sample(void *h, const or_render *r, int lam, int64_t pixel, int s, double *rec);
 
+/* Ambient cache construction (texture baking, Sec. 4.4; the paper's supplementary S1.4 is not
+ * available, this is the reading): for cell (ix, iy, iz) of a res^3 grid over [bmin, bmax],
+ * centre x = bmin + (i + 0.5) (bmax - bmin) / res, and channel c,
+ *   E_c(x) = pi / spp * sum_s L_c(y_s -> x),
+ * directions w_s uniform on the sphere (cos theta = 1 - 2 u0, phi = 2 pi u1 from the path draw of
+ * vertex 0 at pixel index (iy + res iz) res + ix, sample s, wavelength index c), y_s the first hit
+ * along w_s, L_c the incoherent radiance leaving y_s towards x (emission at full weight, NEE + BSDF
+ * with MIS, vertices counted from 1 at y_s up to max_depth, no cache); a miss gives 0.  For
+ * isotropic incident radiance this is the irradiance (pi L).  cells: linear indices
+ * (iz res + iy) res + ix; E: [n_cells][3].  Returns 0 or < 0. */
+typedef struct {
+    int32_t res;
+    double bmin[3], bmax[3];
+    int32_t spp, max_depth;
+    uint64_t seed;
+} or_bake_desc;
+int or_bake(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, int n_threads);
+
 /* building blocks exposed for the pins */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void or_cone_dir(double lambda, double pitch, double u0, double u1, double d[3], double *pdf);

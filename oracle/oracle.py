@@ -53,6 +53,11 @@ class OrRender(C.Structure):
                 ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("grf_phi", C.c_void_p)]
 
 
+class OrBake(C.Structure):
+    _fields_ = [("res", C.c_int32), ("bmin", C.c_double * 3), ("bmax", C.c_double * 3), ("spp", C.c_int32),
+                ("max_depth", C.c_int32), ("seed", C.c_uint64)]
+
+
 REC_FIELDS = ["L", "beta", "opl", "r", "cos", "cosP", "vP", "Px", "Py", "Pz", "tri", "flags",
               "re", "im", "nrays", "u0", "Qx", "Qy"]
 
@@ -71,6 +76,8 @@ def _load():
             lib.or_sample.restype = C.c_int
             lib.or_sample.argtypes = [C.c_void_p, C.POINTER(OrRender), C.c_int, C.c_int64, C.c_int, C.c_void_p]
             lib.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_bake.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int]
+            lib.or_bake.restype = C.c_int
             lib.or_grf_phases.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
             lib.or_grf_phases.restype = None
             lib.or_cone_dir.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
@@ -190,6 +197,22 @@ class Oracle:
             raise ValueError(f"or_trace failed: {rc}")
         U = out[..., 0] + 1j * out[..., 1]
         return (U, flags, sens) if with_flags else U
+
+    def bake(self, res, bmin, bmax, spp, max_depth, seed=1, cells=None, n_threads=None):
+        """Ambient cache E [n_cells][3] (float64) at the listed cell indices (all by default)."""
+        if cells is None:
+            cells = np.arange(res ** 3, dtype=np.int64)
+        cells = np.ascontiguousarray(cells, np.int64)
+        d = OrBake()
+        d.res, d.spp, d.max_depth, d.seed = int(res), int(spp), int(max_depth), int(seed)
+        for k in range(3):
+            d.bmin[k], d.bmax[k] = float(bmin[k]), float(bmax[k])
+        E = np.zeros((len(cells), 3), np.float64)
+        rc = self._lib.or_bake(self._h, C.byref(d), cells.ctypes.data, len(cells), E.ctypes.data,
+                               int(n_threads or os.cpu_count() or 1))
+        if rc != 0:
+            raise ValueError(f"or_bake failed: {rc}")
+        return E
 
     def trace_full(self, render, n_threads=None, grf=None):
         U = self.trace(render, None, n_threads, grf=grf)
