@@ -243,6 +243,33 @@ hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, in
                              int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
                              void *stream);
 
+/* ---- ambient cache construction (texture baking, Sec. 4.4) ---------------------------- */
+/* The supplementary section that defines the bake is not available; this is the reading.
+ * For cell (ix, iy, iz) of a res^3 grid over [bmin, bmax] (centre x = bmin + (i + 0.5)
+ * (bmax - bmin) / res) and channel c: E_c(x) = pi / spp * sum_s L_c(y_s -> x), with spp
+ * directions w_s uniform on the sphere (cos theta = 1 - 2 u0, phi = 2 pi u1 from the Philox
+ * path draw of vertex 0 at pixel index (iy + res iz) res + ix, sample s, wavelength index c,
+ * key seed), y_s the first hit along w_s and L_c the incoherent radiance leaving it towards x
+ * (emission at full weight, NEE + BSDF sampling with MIS, vertices counted from 1 at y_s up
+ * to max_depth, no cache); a miss gives 0.  For isotropic incident light E is the irradiance
+ * pi L, the quantity the cache lookup multiplies by albedo / pi.  Writes float [res][res]
+ * [res][3] ([z][y][x][c]) to E_dev (caller-owned device memory, E_bytes >= 12 res^3).
+ * Asynchronous on 'stream'. */
+typedef struct {
+    int32_t res;
+    float bmin[3], bmax[3];
+    int32_t spp, max_depth;
+    uint64_t seed;
+} hpt_bake_desc;
+hpt_status hpt_cache_bake(hpt_ctx *ctx, uint64_t scene_id, const hpt_bake_desc *desc, float *E_dev,
+                          size_t E_bytes, void *stream);
+/* Replace the scene's ambient cache by the float grid E_dev [res][res][res][3] over [bmin,
+ * bmax] (device memory, converted to binary16 with round to nearest even; res = 0 removes
+ * the cache).  Synchronises the device first (traces in flight may read the old cache);
+ * HPT_ERR_BUSY while queued requests use the scene. */
+hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
+                               const float bmax[3], const float *E_dev);
+
 /* ---- serving: continuous batching of render requests ---------------------------------- */
 /* Queue a request; the scheduler thread admits it when a slot and memory are free and runs
  * it concurrently with the requests already on the device.  out_dev is caller-owned and must

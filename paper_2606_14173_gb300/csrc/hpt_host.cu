@@ -18,6 +18,7 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "hpt.h"
@@ -200,6 +201,7 @@ struct Builder {
 // ------------------------------------------------------------------------------ context
 struct SceneRec {
     void *arena = nullptr;
+    void *cache_buf = nullptr;      // a cache set after upload (hpt_scene_set_cache)
     size_t bytes = 0;
     DevScene dev{};
     int n_nodes = 0, depth = 0;
@@ -389,7 +391,10 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     for (auto &w : ctx->inflight) cudaEventDestroy(w.ev);
     for (auto &g : ctx->graphs) free_frame(g);
     for (auto e : ctx->free_events) cudaEventDestroy(e);
-    for (auto &kv : ctx->scenes) cudaFree(kv.second->arena);
+    for (auto &kv : ctx->scenes) {
+        cudaFree(kv.second->arena);
+        if (kv.second->cache_buf) cudaFree(kv.second->cache_buf);
+    }
     for (auto &s : ctx->slots) {
         cudaFree(s.d_table);
         cudaFreeHost(s.h_table);
@@ -685,6 +690,7 @@ extern "C" hpt_status hpt_scene_release(hpt_ctx *ctx, uint64_t scene_id)
     }
     CUDA_TRY(cudaDeviceSynchronize());
     CUDA_TRY(cudaFree(rec->arena));
+    if (rec->cache_buf) CUDA_TRY(cudaFree(rec->cache_buf));
     return HPT_OK;
 }
 
@@ -1166,6 +1172,94 @@ extern "C" hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt
     if (st) return st;
     if (e != cudaSuccess) return fail(HPT_ERR_CUDA, "kernel timing: %s", cudaGetErrorString(e));
     return read_status(ctx);
+}
+
+// ---------------------------------------------------------------------- cache construction
+__global__ void k_to_half(const float *__restrict__ in, unsigned short *__restrict__ out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __half_as_ushort(__float2half_rn(in[i]));
+}
+
+extern "C" hpt_status hpt_cache_bake(hpt_ctx *ctx, uint64_t scene_id, const hpt_bake_desc *b, float *E_dev,
+                                     size_t E_bytes, void *stream)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!b || !E_dev) return fail(HPT_ERR_INVALID_ARG, "desc or E_dev is NULL");
+    if (b->res < 1 || b->res > 1024) return fail(HPT_ERR_INVALID_ARG, "res must be 1..1024");
+    if (b->spp < 1 || b->max_depth < 1 || b->max_depth > 64) return fail(HPT_ERR_INVALID_ARG, "bad spp or max_depth");
+    for (int k = 0; k < 3; ++k)
+        if (!(b->bmax[k] > b->bmin[k]) || !std::isfinite(b->bmin[k]) || !std::isfinite(b->bmax[k]))
+            return fail(HPT_ERR_INVALID_ARG, "need bmin < bmax");
+    const size_t need = (size_t)b->res * b->res * b->res * 3 * sizeof(float);
+    if (E_bytes < need) return fail(HPT_ERR_INVALID_ARG, "E_bytes %zu < %zu", E_bytes, need);
+    // the cells as a res x res^2 image, the channels as three wavelengths
+    hpt_render_desc r;
+    memset(&r, 0, sizeof r);
+    r.W = b->res;
+    r.H = b->res * b->res;
+    r.pitch = 1.0;
+    r.n_lambda = 3;
+    for (int c = 0; c < 3; ++c) {
+        r.lambda[c] = 1.0;
+        r.channel[c] = c;
+    }
+    r.spp = b->spp;
+    r.max_depth = b->max_depth;
+    r.K = 1;
+    r.seed = b->seed;
+    r.phase_mode = HPT_PHASE_ZERO;
+    r.facet_size = 1.0;
+    for (int k = 0; k < 4; ++k) r.T[5 * k] = 1.0;
+    r.precision = HPT_PREC_DF32;
+    DevJob J;
+    st = make_job(ctx, scene_id, &r, nullptr, 0, J, nullptr);
+    if (st) return st;
+    J.kind = 1;
+    J.bake_out = E_dev;
+    for (int k = 0; k < 3; ++k) {
+        J.bake_lo[k] = b->bmin[k];
+        J.bake_h[k] = (b->bmax[k] - b->bmin[k]) / (float)b->res;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return run_jobs(ctx, &J, 1, HPT_PREC_DF32, false, (cudaStream_t)stream);
+}
+
+extern "C" hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
+                                          const float bmax[3], const float *E_dev)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!bmin || !bmax || (res > 0 && !E_dev)) return fail(HPT_ERR_INVALID_ARG, "bmin, bmax or E_dev is NULL");
+    if (res < 0 || res > 1024) return fail(HPT_ERR_INVALID_ARG, "res must be 0..1024");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return fail(HPT_ERR_NOT_FOUND, "unknown scene %llu", (unsigned long long)scene_id);
+    SceneRec *rec = it->second.get();
+    if (rec->users.load() > 0) return fail(HPT_ERR_BUSY, "scene %llu is used by queued requests", (unsigned long long)scene_id);
+    // traces already launched may still read the old cache
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (rec->cache_buf) {
+        CUDA_TRY(cudaFree(rec->cache_buf));
+        rec->cache_buf = nullptr;
+    }
+    if (res > 0) {
+        const size_t n = (size_t)res * res * res * 3;
+        CUDA_TRY(cudaMalloc(&rec->cache_buf, n * sizeof(unsigned short)));
+        k_to_half<<<(int)std::min<size_t>((n + 255) / 256, 152 * 32), 256>>>(E_dev, (unsigned short *)rec->cache_buf, n);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+        rec->dev.cache = (const unsigned short *)rec->cache_buf;
+    }
+    rec->dev.cache_res = res;
+    for (int k = 0; k < 3; ++k) {
+        rec->dev.cache_bmin[k] = bmin[k];
+        rec->dev.cache_bmax[k] = bmax[k];
+    }
+    return HPT_OK;
 }
 
 // ---------------------------------------------------------------------------- autotune

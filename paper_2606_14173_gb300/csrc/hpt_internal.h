@@ -92,6 +92,11 @@ struct DevJob {
     const float *grf;           // phase mode 2: [K][grf_ny][grf_nx] radians
     int grf_nx, grf_ny;
     RC inv_pitch;
+    // kind 1: ambient-cache bake; items are (channel, cell) with the cells laid out as a
+    // W = res by H = res^2 image, each path an incoherent ray from the cell centre
+    int kind;
+    float *bake_out;            // [res^3][3] float
+    float bake_lo[3], bake_h[3];
 };
 
 struct JobTable {

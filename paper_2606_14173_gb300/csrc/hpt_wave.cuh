@@ -34,7 +34,7 @@ template <> struct RS<df> {
     static __device__ __forceinline__ void st(void *b, int p, df v) { ((float2 *)b)[p] = make_float2(v.hi, v.lo); }
 };
 
-enum : int { VF_V = 0xFF, VF_PREV_DELTA = 1 << 8, VF_INC_FIRST = 1 << 9, VF_HASP = 1 << 10 };
+enum : int { VF_V = 0xFF, VF_PREV_DELTA = 1 << 8, VF_INC_FIRST = 1 << 9, VF_HASP = 1 << 10, VF_BAKE = 1 << 11 };
 constexpr int Q_FINALIZE = (int)0x80000000;
 
 struct PathId {
@@ -111,6 +111,31 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
     if (p >= wd.n_paths) return;
     const PathId id = path_id(jt, wd, p);
     pb.amp[p] = 0.0f;
+    if (id.J->kind == 1) {
+        // cache bake (a wave of bake jobs only): every path starts as an incoherent ray from its
+        // cell centre in a direction uniform on the sphere, drawn at vertex 0
+        if (p == 0) scr->qcount[0][1] = wd.n_paths;
+        pb.q[1][0][p] = id.valid ? p : (p | Q_FINALIZE);
+        pb.vfl[p] = 0;
+        pb.L[p] = 0.0f;
+        pb.nee[p] = 0.0f;
+        if (!id.valid) return;
+        const DevJob &J = *id.J;
+        const float4 u = path_draw(J, id.pix, (unsigned)id.s, 0u, 0u, (unsigned)id.lam);
+        const float ct = 1.0f - 2.0f * u.x, st = 2.0f * sqrtf(u.x * (1.0f - u.x));
+        float sp, cp;
+        sincospif(2.0f * u.y, &sp, &cp);
+        const int iy = id.py % J.W, iz = id.py / J.W;
+        const float3 x = f3(J.bake_lo[0] + ((float)id.px + 0.5f) * J.bake_h[0], J.bake_lo[1] + ((float)iy + 0.5f) * J.bake_h[1],
+                            J.bake_lo[2] + ((float)iz + 0.5f) * J.bake_h[2]);
+        pb.ray_o[p] = make_float4(x.x, x.y, x.z, 1e30f);
+        pb.ray_d[p] = make_float4(st * cp, st * sp, ct, __int_as_float(-1));
+        pb.beta[p] = 1.0f;
+        pb.ppdf[p] = 0.0f;
+        pb.tprev[p] = 0.0f;
+        pb.vfl[p] = VF_PREV_DELTA | VF_BAKE;
+        return;
+    }
     // the first coherent queue is the identity; paths of pixels outside a ragged SLM are marked
     if (p == 0) scr->qcount[0][0] = wd.n_paths;
     pb.q[0][0][p] = id.valid ? p : (p | Q_FINALIZE);
@@ -614,14 +639,16 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
             }
             if (!do_vertex) {
                 if (STATS) cnt.samples++;
-                pb.amp[p] = (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
+                pb.amp[p] = (st.vfl & VF_BAKE) ? st.L
+                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
             }
         }
         if (do_vertex) {
             const bool done = vertex(id, st, S, wo, pb, p, qn, qcn);
             if (done) {
                 if (STATS) cnt.samples++;
-                pb.amp[p] = (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
+                pb.amp[p] = (st.vfl & VF_BAKE) ? st.L
+                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
             } else {
                 pb.L[p] = st.L;
                 pb.beta[p] = st.beta;
@@ -705,6 +732,17 @@ __global__ void __launch_bounds__(ACCUM_BLOCK) k_accum(const JobTable *__restric
     decode_item(jt->jobs + g.job, g.item_begin + il, id);
     if (!id.valid) return;
     const DevJob &J = *id.J;
+    if (J.kind == 1) {
+        // cache bake: E = pi / N sum of the arriving radiance, Kahan-compensated in sample order
+        float a = 0.0f, c = 0.0f;
+        for (int s = 0; s < g.spp; ++s) {
+            const float y = pb.amp[g.path_offset + s * g.item_count + il] - c, t = a + y;
+            c = (t - a) - y;
+            a = t;
+        }
+        J.bake_out[(size_t)id.pix * 3 + id.lam] = 3.14159265f * (a - c) / (float)g.spp;
+        return;
+    }
     const int K = J.K, off = J.hologram_offset, spp = g.spp;
     float ar[KMAX], ai[KMAX], cr[KMAX], ci[KMAX];
 #pragma unroll

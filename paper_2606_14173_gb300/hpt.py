@@ -25,7 +25,7 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
            "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
-           "hpt_asm_propagate"]
+           "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -65,6 +65,11 @@ class RenderDesc(C.Structure):
                 ("grf_nx", C.c_int32), ("grf_ny", C.c_int32)]
 
 
+class BakeDesc(C.Structure):
+    _fields_ = [("res", C.c_int32), ("bmin", C.c_float * 3), ("bmax", C.c_float * 3), ("spp", C.c_int32),
+                ("max_depth", C.c_int32), ("seed", C.c_uint64)]
+
+
 _lib = None
 
 
@@ -88,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_cache_bake.argtypes = [vp, C.c_uint64, C.POINTER(BakeDesc), vp, C.c_size_t, vp]
+    lib.hpt_scene_set_cache.argtypes = [vp, C.c_uint64, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
     lib.hpt_grf_build.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, vp]
     lib.hpt_asm_propagate.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.c_double, C.c_double, vp]
@@ -254,6 +261,30 @@ class Context:
         n = (C.c_uint32 * len(KERNEL_NAMES))()
         _check(self.lib.hpt_trace_timed(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, ms, n))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def cache_bake(self, sid: int, res: int, bmin, bmax, spp: int, max_depth: int, seed: int = 1, stream=None):
+        """Ambient cache E [res][res][res][3] (float32 CUDA tensor, [z][y][x][c]) of the scene."""
+        import torch
+        E = torch.empty((res, res, res, 3), dtype=torch.float32, device=f"cuda:{self.device}")
+        d = BakeDesc()
+        d.res, d.spp, d.max_depth, d.seed = int(res), int(spp), int(max_depth), int(seed)
+        for k in range(3):
+            d.bmin[k], d.bmax[k] = float(bmin[k]), float(bmax[k])
+        _check(self.lib.hpt_cache_bake(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(E.data_ptr()),
+                                       E.numel() * 4, _stream_ptr(stream)))
+        return E
+
+    def set_cache(self, sid: int, E, bmin, bmax):
+        """Replace the scene's ambient cache by the float32 CUDA tensor E [res][res][res][3] (None: remove)."""
+        lo = (C.c_float * 3)(*[float(x) for x in bmin])
+        hi = (C.c_float * 3)(*[float(x) for x in bmax])
+        if E is None:
+            _check(self.lib.hpt_scene_set_cache(self.h, C.c_uint64(sid), 0, lo, hi, None))
+            return
+        if not (E.is_cuda and E.dtype.is_floating_point and E.element_size() == 4 and E.is_contiguous()
+                and E.dim() == 4 and E.shape[0] == E.shape[1] == E.shape[2] and E.shape[3] == 3):
+            raise ValueError("E must be a contiguous float32 CUDA tensor [res][res][res][3]")
+        _check(self.lib.hpt_scene_set_cache(self.h, C.c_uint64(sid), int(E.shape[0]), lo, hi, C.c_void_p(E.data_ptr())))
 
     def grf_build(self, phase_seed: int, K: int, nx: int, ny: int, pitch: float, hologram_offset: int = 0,
                   stream=None):

@@ -47,6 +47,7 @@ int main(void) {
   printf("%d %d %d %d\n", HPT_NCOUNTERS, HPT_NKERNELS, HPT_K_TRACE, HPT_K_ACCUM);
   printf("%zu %zu %zu %d\n", offsetof(hpt_render_desc, grf_phi), offsetof(hpt_render_desc, grf_nx),
          offsetof(hpt_render_desc, grf_ny), HPT_PHASE_GRF);
+  printf("%zu %zu %zu\n", sizeof(hpt_bake_desc), offsetof(hpt_bake_desc, spp), offsetof(hpt_bake_desc, seed));
   return 0;
 }
 '''
@@ -62,7 +63,8 @@ int main(void) {
            hpt.RenderDesc.seed.offset, hpt.RenderDesc.T.offset, hpt.RenderDesc.precision.offset,
            hpt.RenderDesc.use_cache.offset, hpt.NCOUNTERS, len(hpt.KERNEL_NAMES),
            hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum"),
-           hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF]
+           hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF,
+           C.sizeof(hpt.BakeDesc), hpt.BakeDesc.spp.offset, hpt.BakeDesc.seed.offset]
     assert [int(x) for x in out] == got
 
 
