@@ -83,3 +83,34 @@ def asm_propagate(U: np.ndarray, pitch: float, lambdas, z: float, K: int | None 
         Q = asm_periodic(P, pitch, lam, z)
         res[f] = Q[oy:oy + H, ox:ox + W]
     return out.reshape(lead + (H, W))
+
+
+# ---------------------------------------------------------------------------------------------
+# Phase-only encoding with complex supervision (Sec. 2 and 5): gradient descent on the SLM
+# phase phi so that the field exp(i phi) propagated by z matches the complex target T up to the
+# phase-shift-invariant scale s = <A, T> / <A, A> (the least-squares complex factor, which
+# absorbs a global amplitude and phase).  Loss L = sum |s A - T|^2 with A = P_z(exp(i phi));
+# at the optimal s, dL/dphi = -2 Im(u conj(G)) with u = exp(i phi) and G = P_z^H(conj(s) R),
+# R = s A - T, and P_z^H the same padded ASM over -z (the transfer function is unitary on the
+# propagating components).  The supplementary section with the optimiser's details is not
+# available: plain gradient descent with a fixed step is the reading.
+# ---------------------------------------------------------------------------------------------
+def encode_loss_grad(phi, T, pitch, lam, z):
+    """(loss, gradient, s) of the complex-supervised phase-only objective at phi [H][W]."""
+    u = np.exp(1j * phi)
+    A = asm_propagate(u[None, None], pitch, [lam], z)[0, 0]
+    s = np.vdot(A, T) / np.vdot(A, A)
+    R = s * A - T
+    G = asm_propagate((np.conj(s) * R)[None, None], pitch, [lam], -z)[0, 0]
+    return float(np.sum(np.abs(R) ** 2)), -2.0 * np.imag(u * np.conj(G)), s
+
+
+def encode(phi0, T, pitch, lam, z, iters, lr):
+    """iters gradient steps phi <- phi - lr dL/dphi from phi0; returns (phi, losses before each step)."""
+    phi = np.array(phi0, np.float64)
+    losses = []
+    for _ in range(iters):
+        L, g, _ = encode_loss_grad(phi, T, pitch, lam, z)
+        losses.append(L)
+        phi = phi - lr * g
+    return phi, np.array(losses)

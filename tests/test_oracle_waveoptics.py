@@ -147,3 +147,50 @@ def test_trace_with_grf_maps(oracle_mod, wo):
         jx = math.floor(a["Qx"] / rg.pitch + nx / 2) % nx
         got = np.angle((b["re"] + 1j * b["im"]) / (a["re"] + 1j * a["im"]))
         assert abs(np.angle(np.exp(1j * (got - 0.37 * jx)))) < 1e-9
+
+
+def _target(wo, rng, W, H, p, lam, z):
+    phi = rng.uniform(-math.pi, math.pi, (H, W))
+    return wo.asm_propagate(np.exp(1j * phi)[None, None], p, [lam], z)[0, 0], phi
+
+
+def test_encode_gradient_is_the_derivative(wo):
+    """Central finite differences of the loss at a few pixels equal the analytic gradient
+    (pins the adjoint ASM, the Wirtinger factor and the sign)."""
+    rng = np.random.default_rng(1)
+    W, H, p, lam, z = 24, 16, 8e-6, 520e-9, 2e-3
+    T = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+    phi = rng.uniform(-math.pi, math.pi, (H, W))
+    L0, g, _ = wo.encode_loss_grad(phi, T, p, lam, z)
+    h = 1e-6
+    for (y, x) in [(0, 0), (5, 17), (15, 23), (8, 3)]:
+        e = np.zeros_like(phi)
+        e[y, x] = h
+        fd = (wo.encode_loss_grad(phi + e, T, p, lam, z)[0] - wo.encode_loss_grad(phi - e, T, p, lam, z)[0]) / (2 * h)
+        assert abs(fd - g[y, x]) <= 1e-6 * max(1.0, abs(fd)), (y, x, fd, g[y, x])
+
+
+def test_encode_scale_is_phase_shift_invariant(wo):
+    """A global phase of the target changes nothing, a global amplitude c scales the loss and
+    its gradient by |c|^2 (the scale factor absorbs both; with the step divided by |c|^2 the
+    iterates are the same)."""
+    rng = np.random.default_rng(2)
+    W, H, p, lam, z = 20, 12, 8e-6, 638e-9, 3e-3
+    T, _ = _target(wo, rng, W, H, p, lam, z)
+    phi0 = rng.uniform(-math.pi, math.pi, (H, W))
+    a, la = wo.encode(phi0, T, p, lam, z, 5, 0.05)
+    b, lb = wo.encode(phi0, T * np.exp(1.1j), p, lam, z, 5, 0.05)
+    assert np.max(np.abs(a - b)) < 1e-9 and np.allclose(lb, la, rtol=1e-9)
+    c, lc = wo.encode(phi0, T * 0.3, p, lam, z, 5, 0.05 / 0.09)
+    assert np.max(np.abs(a - c)) < 1e-9 and np.allclose(lc, la * 0.09, rtol=1e-9)
+
+
+def test_encode_descends_towards_a_reachable_target(wo):
+    """A target made by propagating a phase-only field is reachable: the loss falls steadily."""
+    rng = np.random.default_rng(3)
+    W, H, p, lam, z = 32, 32, 8e-6, 520e-9, 1e-3
+    T, _ = _target(wo, rng, W, H, p, lam, z)
+    phi0 = rng.uniform(-math.pi, math.pi, (H, W))
+    lr = 0.1 / float(np.sum(np.abs(T) ** 2) / (W * H))
+    _, L = wo.encode(phi0, T, p, lam, z, 60, lr)
+    assert np.all(np.diff(L) <= 1e-12 * L[0]) and L[-1] < 0.5 * L[0]
