@@ -243,6 +243,19 @@ hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, in
                              int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
                              void *stream);
 
+/* Phase-only encoding with complex supervision (Sec. 2, Sec. 5 "Phase-only Hologram
+ * Encoding"): 'iters' gradient steps phi <- phi - lr dL/dphi on the SLM phase phi_dev (float
+ * [H][W] radians, device, read as the start and overwritten), L = sum |s A - T|^2 with
+ * A = ASM_z(exp(i phi)) (the padded propagation of hpt_asm_propagate), T = target_dev
+ * (complex64 [H][W], device) and s = <A, T> / <A, A> the phase-shift-invariant complex scale;
+ * dL/dphi = -2 Im(exp(i phi) conj(ASM_-z(conj(s) (s A - T)))).  The supplementary section with
+ * the paper's optimiser is not available: plain gradient descent with a fixed step is the
+ * reading.  losses: host array of iters doubles (L before each step) or NULL; when given the
+ * call waits for the stream.  Reductions in double. */
+hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, float *phi_dev, int32_t W, int32_t H,
+                            double lambda, double pitch, double z, int32_t iters, float lr, double *losses,
+                            void *stream);
+
 /* ---- ambient cache construction (texture baking, Sec. 4.4) ---------------------------- */
 /* The supplementary section that defines the bake is not available; this is the reading.
  * For cell (ix, iy, iz) of a res^3 grid over [bmin, bmax] (centre x = bmin + (i + 0.5)

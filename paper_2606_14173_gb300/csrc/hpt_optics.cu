@@ -8,6 +8,7 @@
 // from double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
 // ~1e5 turns, is formed in double before its fraction is taken.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -339,6 +340,145 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     return HPT_OK;
 }
 
+namespace {
+
+// One padded angular-spectrum step of a W x H field: the sizes and the scratch it needs.
+struct AsmPlan {
+    int W, H, Wp, Hp, lx, ly, ox, oy;
+    float2 *A, *B, *twx, *twy;
+};
+
+cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, const float2 *Ht, cudaStream_t s)
+{
+    // rows of the padded field -> transpose -> per-frequency rows: FFT, transfer, inverse FFT
+    // -> transpose -> inverse FFT of the window's rows, cropped
+    const dim3 tb(32, 8);
+    k_asm_rows_in<<<std::min(P.Hp, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Wp / 4)), 2 * sizeof(float2) * P.Wp,
+                    s>>>(in, P.A, P.lx, P.Hp, P.W, P.H, P.ox, P.oy, P.twx);
+    k_transpose<<<dim3((P.Wp + 31) / 32, (P.Hp + 31) / 32), tb, 0, s>>>(P.A, P.B, P.Wp, P.Hp);
+    k_asm_rows_conv<<<std::min(P.Wp, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Hp / 4)),
+                      2 * sizeof(float2) * P.Hp, s>>>(P.B, P.ly, P.Wp, Ht, P.twy);
+    k_transpose<<<dim3((P.Hp + 31) / 32, (P.Wp + 31) / 32), tb, 0, s>>>(P.B, P.A, P.Hp, P.Wp);
+    k_asm_rows_out<<<std::min(P.H, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Wp / 4)), 2 * sizeof(float2) * P.Wp,
+                     s>>>(P.A, out, P.lx, P.W, P.H, P.ox, P.oy, P.twx);
+    return cudaGetLastError();
+}
+
+bool asm_sizes(int W, int H, AsmPlan &P)
+{
+    P.W = W;
+    P.H = H;
+    P.Wp = P.Hp = 1;
+    while (P.Wp < 2 * W) P.Wp <<= 1;
+    while (P.Hp < 2 * H) P.Hp <<= 1;
+    if (!pow2_in_range(P.Wp) || !pow2_in_range(P.Hp)) return false;
+    P.lx = ilog2(P.Wp);
+    P.ly = ilog2(P.Hp);
+    P.ox = (P.Wp - W) / 2;
+    P.oy = (P.Hp - H) / 2;
+    return true;
+}
+
+// ---- phase-only encoding -----------------------------------------------------------------
+constexpr int RED_BLOCKS = 304, RED_THREADS = 256;
+
+__global__ void k_phase_field(const float *__restrict__ phi, float2 *__restrict__ u, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float sn, cs;
+        sincosf(phi[i], &sn, &cs);
+        u[i] = make_float2(cs, sn);
+    }
+}
+
+// per-block partial sums (double) of <A, T> = sum conj(A) T and <A, A>
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const float2 *__restrict__ A, const float2 *__restrict__ T, size_t n,
+                                                      double *__restrict__ part)
+{
+    __shared__ double sre[RED_THREADS], sim[RED_THREADS], saa[RED_THREADS];
+    double re = 0.0, im = 0.0, aa = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = A[i], t = T[i];
+        re += (double)a.x * t.x + (double)a.y * t.y;
+        im += (double)a.x * t.y - (double)a.y * t.x;
+        aa += (double)a.x * a.x + (double)a.y * a.y;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    saa[threadIdx.x] = aa;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sre[threadIdx.x] += sre[threadIdx.x + o];
+            sim[threadIdx.x] += sim[threadIdx.x + o];
+            saa[threadIdx.x] += saa[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = sre[0];
+        part[3 * blockIdx.x + 1] = sim[0];
+        part[3 * blockIdx.x + 2] = saa[0];
+    }
+}
+
+// s = <A, T> / <A, A>, from the partial sums in a fixed order
+__global__ void k_scale(const double *__restrict__ part, int nb, double *__restrict__ sc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double re = 0.0, im = 0.0, aa = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        re += part[3 * b];
+        im += part[3 * b + 1];
+        aa += part[3 * b + 2];
+    }
+    sc[0] = aa > 0.0 ? re / aa : 0.0;
+    sc[1] = aa > 0.0 ? im / aa : 0.0;
+}
+
+// V = conj(s) (s A - T), with per-block partial sums of |s A - T|^2
+__global__ void __launch_bounds__(RED_THREADS) k_residual(const float2 *__restrict__ A, const float2 *__restrict__ T,
+                                                          const double *__restrict__ sc, float2 *__restrict__ V, size_t n,
+                                                          double *__restrict__ part)
+{
+    __shared__ double sl[RED_THREADS];
+    const float sr = (float)sc[0], si = (float)sc[1];
+    double l = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = A[i], t = T[i];
+        const float rr = sr * a.x - si * a.y - t.x, ri = sr * a.y + si * a.x - t.y;
+        l += (double)rr * rr + (double)ri * ri;
+        V[i] = make_float2(sr * rr + si * ri, sr * ri - si * rr);
+    }
+    sl[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sl[threadIdx.x] += sl[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sl[0];
+}
+
+__global__ void k_loss(const double *__restrict__ part, int nb, double *__restrict__ loss)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double l = 0.0;
+    for (int b = 0; b < nb; ++b) l += part[b];
+    *loss = l;
+}
+
+// phi <- phi - lr dL/dphi, dL/dphi = -2 Im(u conj(G))
+__global__ void k_phase_step(float *__restrict__ phi, const float2 *__restrict__ u, const float2 *__restrict__ G, size_t n,
+                             float lr)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = u[i], g = G[i];
+        phi[i] += 2.0f * lr * (a.y * g.x - a.x * g.y);
+    }
+}
+
+}  // namespace
+
 extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, int32_t W, int32_t H,
                                         int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
                                         void *stream)
@@ -348,11 +488,9 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     if (!in_dev || !out_dev || !lambdas) return internal_fail(HPT_ERR_INVALID_ARG, "in_dev, out_dev or lambdas is NULL");
     if (W < 1 || H < 1 || n_lambda < 1 || n_lambda > 3 || K < 1)
         return internal_fail(HPT_ERR_INVALID_ARG, "need W, H, K >= 1 and 1 <= n_lambda <= 3");
-    int Wp = 1, Hp = 1;
-    while (Wp < 2 * W) Wp <<= 1;
-    while (Hp < 2 * H) Hp <<= 1;
-    if (!pow2_in_range(Wp) || !pow2_in_range(Hp))
-        return internal_fail(HPT_ERR_UNSUPPORTED, "padded size above 8192 x 8192 (W, H <= 4096)");
+    AsmPlan P;
+    if (!asm_sizes(W, H, P)) return internal_fail(HPT_ERR_UNSUPPORTED, "padded size above 8192 x 8192 (W, H <= 4096)");
+    const int Wp = P.Wp, Hp = P.Hp;
     if (!(pitch > 0.0)) return internal_fail(HPT_ERR_INVALID_ARG, "pitch must be > 0");
     for (int l = 0; l < n_lambda; ++l)
         if (!(lambdas[l] > 0.0)) return internal_fail(HPT_ERR_INVALID_ARG, "wavelengths must be > 0");
@@ -363,31 +501,77 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     const size_t bytes = (2 + (size_t)n_lambda) * np * sizeof(float2) + (size_t)(Wp + Hp) * sizeof(float2);
     char *buf = nullptr;
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
-    float2 *A = (float2 *)buf, *B = A + np, *Hf = B + np, *twx = Hf + (size_t)n_lambda * np, *twy = twx + Wp;
-    const int ox = (Wp - W) / 2, oy = (Hp - H) / 2;
+    P.A = (float2 *)buf;
+    P.B = P.A + np;
+    float2 *Hf = P.B + np;
+    P.twx = Hf + (size_t)n_lambda * np;
+    P.twy = P.twx + Wp;
     cudaError_t e = cudaSuccess;
-    k_twiddles<<<(Wp + 255) / 256, 256, 0, s>>>(twx, Wp);
-    k_twiddles<<<(Hp + 255) / 256, 256, 0, s>>>(twy, Hp);
+    k_twiddles<<<(Wp + 255) / 256, 256, 0, s>>>(P.twx, Wp);
+    k_twiddles<<<(Hp + 255) / 256, 256, 0, s>>>(P.twy, Hp);
     for (int l = 0; l < n_lambda; ++l)
         k_transfer<<<grid_for(np), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, pitch, lambdas[l], z, 1.0f / (float)np);
     const float2 *in = (const float2 *)in_dev;
     float2 *out = (float2 *)out_dev;
-    const int lx = ilog2(Wp), ly = ilog2(Hp);
-    const dim3 tb(32, 8);
     for (int f = 0; f < n_lambda * K && e == cudaSuccess; ++f) {
         const size_t fo = (size_t)f * W * H;
-        // rows of the padded field -> transpose -> per-frequency rows: FFT, transfer, inverse
-        // FFT -> transpose -> inverse FFT of the window's rows, cropped
-        k_asm_rows_in<<<std::min(Hp, 152 * 8), std::min(FFT_THREADS, std::max(32, Wp / 4)), 2 * sizeof(float2) * Wp, s>>>(
-            in + fo, A, lx, Hp, W, H, ox, oy, twx);
-        k_transpose<<<dim3((Wp + 31) / 32, (Hp + 31) / 32), tb, 0, s>>>(A, B, Wp, Hp);
-        k_asm_rows_conv<<<std::min(Wp, 152 * 8), std::min(FFT_THREADS, std::max(32, Hp / 4)), 2 * sizeof(float2) * Hp, s>>>(
-            B, ly, Wp, Hf + (size_t)(f / K) * np, twy);
-        k_transpose<<<dim3((Hp + 31) / 32, (Wp + 31) / 32), tb, 0, s>>>(B, A, Hp, Wp);
-        k_asm_rows_out<<<std::min(H, 152 * 8), std::min(FFT_THREADS, std::max(32, Wp / 4)), 2 * sizeof(float2) * Wp, s>>>(
-            A, out + fo, lx, W, H, ox, oy, twx);
+        e = asm_field(P, in + fo, out + fo, Hf + (size_t)(f / K) * np, s);
+    }
+    cudaError_t e2 = cudaFreeAsync(buf, s);
+    OPT_TRY(e);
+    OPT_TRY(e2);
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, float *phi_dev, int32_t W, int32_t H,
+                                       double lambda, double pitch, double z, int32_t iters, float lr, double *losses,
+                                       void *stream)
+{
+    hpt_status st = internal_check(ctx);
+    if (st) return st;
+    if (!target_dev || !phi_dev) return internal_fail(HPT_ERR_INVALID_ARG, "target_dev or phi_dev is NULL");
+    if (W < 1 || H < 1 || iters < 0) return internal_fail(HPT_ERR_INVALID_ARG, "need W, H >= 1 and iters >= 0");
+    if (!(pitch > 0.0) || !(lambda > 0.0) || !std::isfinite(z) || !std::isfinite(lr))
+        return internal_fail(HPT_ERR_INVALID_ARG, "bad pitch, lambda, z or lr");
+    AsmPlan P;
+    if (!asm_sizes(W, H, P)) return internal_fail(HPT_ERR_UNSUPPORTED, "padded size above 8192 x 8192 (W, H <= 4096)");
+    OPT_TRY(cudaSetDevice(internal_ctx_device(ctx)));
+    OPT_TRY(fft_setup());
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = (size_t)P.Wp * P.Hp, n = (size_t)W * H;
+    const size_t bytes = 4 * np * sizeof(float2) + (size_t)(P.Wp + P.Hp) * sizeof(float2) + 3 * n * sizeof(float2) +
+                         (3 * RED_BLOCKS + 2 + (size_t)std::max(iters, 1)) * sizeof(double);
+    char *buf = nullptr;
+    OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
+    P.A = (float2 *)buf;
+    P.B = P.A + np;
+    float2 *Hp_ = P.B + np, *Hm = Hp_ + np;          // transfer over +z and over -z (the adjoint)
+    P.twx = Hm + np;
+    P.twy = P.twx + P.Wp;
+    float2 *U = P.twy + P.Hp, *Afield = U + n, *V = Afield + n;
+    double *part = (double *)(V + n), *sc = part + 3 * RED_BLOCKS, *dloss = sc + 2;
+    const float2 *T = (const float2 *)target_dev;
+    k_twiddles<<<(P.Wp + 255) / 256, 256, 0, s>>>(P.twx, P.Wp);
+    k_twiddles<<<(P.Hp + 255) / 256, 256, 0, s>>>(P.twy, P.Hp);
+    k_transfer<<<grid_for(np), 256, 0, s>>>(Hp_, P.Wp, P.Hp, pitch, lambda, z, 1.0f / (float)np);
+    k_transfer<<<grid_for(np), 256, 0, s>>>(Hm, P.Wp, P.Hp, pitch, lambda, -z, 1.0f / (float)np);
+    cudaError_t e = cudaGetLastError();
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        k_phase_field<<<grid_for(n), 256, 0, s>>>(phi_dev, U, n);
+        e = asm_field(P, U, Afield, Hp_, s);
+        if (e != cudaSuccess) break;
+        k_dots<<<RED_BLOCKS, RED_THREADS, 0, s>>>(Afield, T, n, part);
+        k_scale<<<1, 32, 0, s>>>(part, RED_BLOCKS, sc);
+        k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(Afield, T, sc, V, n, part);
+        k_loss<<<1, 32, 0, s>>>(part, RED_BLOCKS, dloss + it);
+        e = asm_field(P, V, V, Hm, s);
+        if (e != cudaSuccess) break;
+        k_phase_step<<<grid_for(n), 256, 0, s>>>(phi_dev, U, V, n, lr);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && losses && iters > 0)
+        e = cudaMemcpyAsync(losses, dloss, sizeof(double) * iters, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && losses && iters > 0) e = cudaStreamSynchronize(s);
     cudaError_t e2 = cudaFreeAsync(buf, s);
     OPT_TRY(e);
     OPT_TRY(e2);

@@ -25,7 +25,7 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
            "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
-           "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache"]
+           "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache", "hpt_phase_encode"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_phase_encode.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                     C.c_float, C.POINTER(C.c_double), vp]
     lib.hpt_cache_bake.argtypes = [vp, C.c_uint64, C.POINTER(BakeDesc), vp, C.c_size_t, vp]
     lib.hpt_scene_set_cache.argtypes = [vp, C.c_uint64, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
     lib.hpt_grf_build.argtypes = [vp, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, vp]
@@ -261,6 +263,22 @@ class Context:
         n = (C.c_uint32 * len(KERNEL_NAMES))()
         _check(self.lib.hpt_trace_timed(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, ms, n))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def phase_encode(self, target, phi, lam: float, pitch: float, z: float, iters: int, lr: float, stream=None):
+        """Gradient steps on phi (float32 CUDA tensor [H][W], updated in place) towards the complex
+        target (complex64 CUDA tensor [H][W]); returns the loss before each step."""
+        if not (target.is_cuda and target.dtype.is_complex and target.element_size() == 8 and target.is_contiguous()
+                and target.dim() == 2):
+            raise ValueError("target must be a contiguous complex64 CUDA tensor [H][W]")
+        if not (phi.is_cuda and phi.dtype.is_floating_point and phi.element_size() == 4 and phi.is_contiguous()
+                and tuple(phi.shape) == tuple(target.shape)):
+            raise ValueError("phi must be a contiguous float32 CUDA tensor of the target's shape")
+        H, W = (int(x) for x in target.shape)
+        losses = (C.c_double * max(int(iters), 1))()
+        _check(self.lib.hpt_phase_encode(self.h, C.c_void_p(target.data_ptr()), C.c_void_p(phi.data_ptr()), W, H,
+                                         float(lam), float(pitch), float(z), int(iters), float(lr), losses,
+                                         _stream_ptr(stream)))
+        return np.array(losses[:int(iters)])
 
     def cache_bake(self, sid: int, res: int, bmin, bmax, spp: int, max_depth: int, seed: int = 1, stream=None):
         """Ambient cache E [res][res][res][3] (float32 CUDA tensor, [z][y][x][c]) of the scene."""

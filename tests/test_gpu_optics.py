@@ -130,3 +130,25 @@ def test_invalid_arguments(ctx, torch_cuda):
     with pytest.raises(hpt.HptError):
         ctx.asm_propagate(U, (-1.0,), 8e-6, 1e-3)
     ctx.sync()
+
+
+@pytest.mark.parametrize("W,H,z", [(160, 120, 2e-3), (300, 37, -1e-3)])
+def test_phase_encode_matches_the_oracle(ctx, wo, torch_cuda, W, H, z):
+    """Gradient descent on the SLM phase under complex supervision: the GPU's iterates and
+    losses follow the oracle's (the same start, target and step)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(W)
+    p, lam, iters = 8e-6, 520e-9, 12
+    T = wo.asm_propagate(np.exp(1j * rng.uniform(-np.pi, np.pi, (H, W)))[None, None], p, [lam], z)[0, 0]
+    T = T + 0.1 * (rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W)))
+    phi0 = rng.uniform(-np.pi, np.pi, (H, W))
+    lr = 0.1 / float(np.mean(np.abs(T) ** 2))
+    Tg = torch.from_numpy(T.astype(np.complex64)).cuda()
+    phi = torch.from_numpy(phi0.astype(np.float32)).cuda()
+    L = ctx.phase_encode(Tg, phi, lam, p, z, iters, lr)
+    ref_phi, ref_L = wo.encode(phi0.astype(np.float32).astype(np.float64), T.astype(np.complex64).astype(np.complex128),
+                               p, lam, z, iters, lr)
+    assert np.all(np.abs(L - ref_L) <= 1e-4 * ref_L), (L, ref_L)
+    d = np.abs(np.angle(np.exp(1j * (phi.cpu().numpy() - ref_phi))))
+    assert d.max() < 1e-3 and np.median(d) < 1e-5
+    assert ref_L[-1] < ref_L[0]
