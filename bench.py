@@ -163,13 +163,26 @@ def barrier(world):
 
 
 def allreduce_max(x, world):
+    """Max over ranks (the timing rule: the slowest replica sets the whole job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Replicas only: every rank renders its own frame of the same workload with its own
+    sampling seed; there is no exchange between ranks on the data path."""
+    return 1 + rank
+
+
+def job_value(samples_per_step, steps, max_ms, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * samples_per_step * steps / (max_ms / 1e3)
 
 
 def cpu_oracle_rate(scene, r, n_pixels, seed=5):
@@ -363,7 +376,7 @@ def main():
     sc = getattr(S, scene_fn)()
     sid = ctx.upload_scene(sc)
     make_render = getattr(S, render_fn)
-    r = make_render(seed=1 + rank, **wl_over)
+    r = make_render(seed=replica_seed(rank), **wl_over)
     samples_per_step = r.path_samples()
     out = hpt.alloc_output(r)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
@@ -375,7 +388,7 @@ def main():
     def step_mixed():
         ctx.trace(sid, r, out, precision=hpt.PREC_DF32, stream=stream)
 
-    r_plain = [make_render(seed=1 + rank, lambdas=(l,), channels=(c,), **wl_over)
+    r_plain = [make_render(seed=replica_seed(rank), lambdas=(l,), channels=(c,), **wl_over)
                for l, c in zip(r.lambdas, r.channels)]
     outs_plain = [hpt.alloc_output(rp) for rp in r_plain]
 
@@ -420,7 +433,7 @@ def main():
     gaps_ms = []
 
     total_ms, launch_ms, clocks = timed(step_mixed, args.steps, args.warmup, sample_clocks=True)
-    value = world * samples_per_step * args.steps / (total_ms / 1e3)
+    value = job_value(samples_per_step, args.steps, total_ms, world)
     holo_per_s = world * r.K * args.steps / (total_ms / 1e3)
 
     plain = None
