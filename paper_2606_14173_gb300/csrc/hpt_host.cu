@@ -105,7 +105,21 @@ struct Builder {
     std::vector<BuildNode> nodes;
     int max_depth_seen = 0;
     // depth <= TSTACK - 1: a near-first traversal then never holds more than TSTACK entries
-    static constexpr int BINS = 32, LEAF_MAX = 4, DEPTH_LIMIT = TSTACK - 1;
+#ifndef HPT_SAH_CT
+#define HPT_SAH_CT 0.5
+#endif
+#ifndef HPT_LEAF_MAX
+#define HPT_LEAF_MAX 2
+#endif
+#ifndef HPT_LEAF_CAP
+#define HPT_LEAF_CAP 4
+#endif
+    // SAH in units of one triangle test: a split costs CT (one node visit) times the node's area
+    // plus the children's area-weighted triangle counts; a leaf costs its area times its count.
+    // Nodes of at most LEAF_MAX triangles are always leaves, nodes of up to LEAF_CAP become
+    // leaves when no split is cheaper.
+    static constexpr int BINS = 32, LEAF_MAX = HPT_LEAF_MAX, LEAF_CAP = HPT_LEAF_CAP, DEPTH_LIMIT = TSTACK - 1;
+    static constexpr double CT = HPT_SAH_CT;
 
     Builder(const std::vector<Box> &pb_, const std::vector<float> &c_, std::vector<int> prims)
         : pb(pb_), cent(c_), idx(std::move(prims)) {}
@@ -163,12 +177,12 @@ struct Builder {
                 acc.grow(bb[k]);
                 n += bc[k];
                 if (ln[k - 1] == 0 || n == 0) continue;
-                double cost = la[k - 1] * ln[k - 1] + acc.area() * n;
+                double cost = CT * b.area() + la[k - 1] * ln[k - 1] + acc.area() * n;
                 if (cost < best_cost) { best_cost = cost; best_axis = ax; best_split = k; }
             }
         }
         double leaf_cost = b.area() * count;
-        if (depth < DEPTH_LIMIT && count <= 255 && (best_axis < 0 || (best_cost >= leaf_cost && count <= 8)))
+        if (depth < DEPTH_LIMIT && count <= 255 && (best_axis < 0 || (best_cost >= leaf_cost && count <= LEAF_CAP)))
             return make_leaf(b, start, count);
         if (depth >= DEPTH_LIMIT) best_axis = -1;   // forced median split of an oversized deep node
         int mid;
