@@ -509,7 +509,9 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
                 const float3 m2f = f3(RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 7)),
                                       RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 8)),
                                       RO::to_f(RO::load(sc.ref64, sc.refdf, rb + 9)));
-                S = make_surf(sc, tri, tof3(P), dot3(m1f, dPf), dot3(m2f, dPf));
+                const float3 Pf = tof3(P);
+                const float bb1 = dot3(m1f, dPf), bb2 = dot3(m2f, dPf);
+                S = make_surf(sc, tri, Pf, bb1, bb2);
                 if (kind != 2 && kind != 3) {
                     // P, the real image point.  For a rigid T the virtual image point
                     // Q = T (O + d_OPL v) lies at distance r = d_OPL from the pixel along the
@@ -539,14 +541,19 @@ __global__ void __launch_bounds__(SHADE_BLOCK) k_shade(const JobTable *__restric
                         pb.cz[p] = RO::floor_i(P.z * ih);
                     }
                     pb.basep[p] = pb.cost[p] * RO::to_f(opl) / (J.pdf_w[id.lam] * cosP * J.lambda_f[id.lam]);
-                    st.L = 0.0f;
-                    st.beta = 1.0f;
-                    st.ppdf = 0.0f;
-                    st.tprev = 0.0f;
-                    st.nee = 0.0f;
-                    st.vfl = cv | VF_PREV_DELTA | VF_INC_FIRST | VF_HASP;
-                    wo = -dl;
-                    do_vertex = true;
+                    // the incoherent part starts at P: handed to this iteration's incoherent
+                    // shading as a hit at distance 0 from P (vertex count cv after its increment),
+                    // so that the coherent kernel carries no BSDF / NEE code
+                    pb.L[p] = 0.0f;
+                    pb.beta[p] = 1.0f;
+                    pb.ppdf[p] = 0.0f;
+                    pb.tprev[p] = 0.0f;
+                    pb.nee[p] = 0.0f;
+                    pb.vfl[p] = (cv - 1) | VF_PREV_DELTA | VF_INC_FIRST | VF_HASP;
+                    pb.ray_o[p] = make_float4(Pf.x, Pf.y, Pf.z, 1e30f);
+                    pb.ray_d[p] = make_float4(dl.x, dl.y, dl.z, __int_as_float(tri));
+                    pb.hit[p] = make_float4(0.0f, bb1, bb2, __int_as_float(tri));
+                    enqueue(pb.q[1][par], &scr->qcount[it][1], p);
                 } else if (cv < J.max_depth) {
                     // delta vertex: shading normal and the new direction in the coherent arithmetic
                     const MatDev M = sc.mats[ix.w];
