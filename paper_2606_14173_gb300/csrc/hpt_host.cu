@@ -252,6 +252,13 @@ struct hpt_ctx {
     // path state of one wave (capacity paths), all wave work runs on wstream
     PathBufs pb{};
     void *pb_arena = nullptr;
+    // second wave lane: consecutive waves of a trace alternate between (pb, d_scr, wstream) and
+    // (pb2, d_scr2, wstream2), so that one wave's kernels fill the other's tails
+    void *pb_arena2 = nullptr;
+    PathBufs pb2{};
+    SlotScratch *d_scr2 = nullptr;
+    cudaStream_t wstream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
     // captured frames of hpt_trace, keyed by what fixes the launch sequence
@@ -355,6 +362,11 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
     CUDA_TRY(cudaMemset(ctx->d_scr, 0, sizeof(SlotScratch)));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream2, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CUDA_TRY(cudaMalloc(&ctx->d_scr2, sizeof(SlotScratch)));
+    CUDA_TRY(cudaMemset(ctx->d_scr2, 0, sizeof(SlotScratch)));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     // cos/sin(2 pi k / 256) split into float pairs for the double-float cone sampler
@@ -417,6 +429,11 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->pb_arena) cudaFree(ctx->pb_arena);
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     if (ctx->wstream) cudaStreamDestroy(ctx->wstream);
+    if (ctx->wstream2) cudaStreamDestroy(ctx->wstream2);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->pb_arena2) cudaFree(ctx->pb_arena2);
+    if (ctx->d_scr2) cudaFree(ctx->d_scr2);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
@@ -830,18 +847,14 @@ static Slot *acquire_slot(hpt_ctx *ctx)
 // bytes of path state per path (see PathBufs)
 static size_t path_bytes() { return 7 * 8 + 3 * 4 + 4 + 6 * 4 + 3 * 16 + 16 + 4 + 3 * 4 + 3 * 4 + 6 * 4; }
 
-static hpt_status ensure_paths(hpt_ctx *ctx)
+static void carve_paths(void *arena, size_t B, PathBufs &b)
 {
-    if (ctx->pb_arena) return HPT_OK;
-    const size_t B = (size_t)ctx->capacity;
-    CUDA_TRY(cudaMalloc(&ctx->pb_arena, B * path_bytes() + 64 * 256));
-    char *p = (char *)ctx->pb_arena;
+    char *p = (char *)arena;
     auto take = [&](size_t bytes) {
         void *r = p;
         p += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    PathBufs &b = ctx->pb;
     for (int k = 0; k < 3; ++k) b.co[k] = take(8 * B);
     for (int k = 0; k < 3; ++k) b.cd[k] = take(8 * B);
     b.opl = take(8 * B);
@@ -869,6 +882,22 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
     for (int k = 0; k < 3; ++k)
         for (int j = 0; j < 2; ++j) b.q[k][j] = (int *)take(4 * B);
     b.capacity = (int)B;
+}
+
+static hpt_status ensure_paths(hpt_ctx *ctx)
+{
+    if (ctx->pb_arena) return HPT_OK;
+    const size_t B = (size_t)ctx->capacity;
+    CUDA_TRY(cudaMalloc(&ctx->pb_arena, B * path_bytes() + 64 * 256));
+    cudaError_t e = cudaMalloc(&ctx->pb_arena2, B * path_bytes() + 64 * 256);
+    if (e != cudaSuccess) {
+        cudaFree(ctx->pb_arena);
+        ctx->pb_arena = nullptr;
+        ctx->pb_arena2 = nullptr;
+        return fail(HPT_ERR_OOM, "wave state: %s", cudaGetErrorString(e));
+    }
+    carve_paths(ctx->pb_arena, B, ctx->pb);
+    carve_paths(ctx->pb_arena2, B, ctx->pb2);
     return HPT_OK;
 }
 
@@ -883,6 +912,11 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     memset(&wd, 0, sizeof wd);
     int max_depth = 1;
     hpt_status st = HPT_OK;
+    // waves alternate between two lanes (path state, scratch, stream); the second lane forks
+    // from ws at the start and joins ws at the end.  Per-kernel timing keeps one lane.
+    const bool two_lanes = ctx->timer == nullptr;
+    int n_waves = 0;
+    bool forked = false;
     auto mark = [&](int kind) -> cudaError_t {
         hpt_ctx::KernelTimer *tm = ctx->timer;
         if (!tm) return cudaSuccess;
@@ -898,25 +932,30 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     };
     auto flush = [&]() -> hpt_status {
         if (wd.n_seg == 0) return HPT_OK;
+        const int lane = two_lanes ? (n_waves & 1) : 0;
+        ++n_waves;
+        const PathBufs &pb = lane ? ctx->pb2 : ctx->pb;
+        SlotScratch *scr = lane ? ctx->d_scr2 : ctx->d_scr;
+        cudaStream_t s = lane ? ctx->wstream2 : ws;
         const int n_iter = max_depth + 1;
         CUDA_TRY(mark(HPT_K_GEN));
-        CUDA_TRY(cudaMemsetAsync(ctx->d_scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws));
-        CUDA_TRY(wave_gen(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        CUDA_TRY(cudaMemsetAsync(scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), s));
+        CUDA_TRY(wave_gen(prec, jt, wd, pb, scr, s));
         for (int it = 0; it < n_iter; ++it) {
             CUDA_TRY(mark(HPT_K_TRACE));
-            CUDA_TRY(wave_trace(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_trace[prec], ws));
+            CUDA_TRY(wave_trace(prec, stats, jt, wd, pb, scr, it, ctx->grid_trace[prec], s));
             CUDA_TRY(mark(HPT_K_SHADE));
-            CUDA_TRY(wave_shade(prec, stats, jt, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws));
+            CUDA_TRY(wave_shade(prec, stats, jt, wd, pb, scr, it, ctx->grid_shade[prec], s));
         }
         CUDA_TRY(mark(HPT_K_ACCUM));
-        CUDA_TRY(wave_accum(prec, jt, wd, ctx->pb, ctx->d_scr, ws));
+        CUDA_TRY(wave_accum(prec, jt, wd, pb, scr, s));
         CUDA_TRY(mark(-1));
         if (allow_debug && ctx->debug_waves > 0) {
             // diagnostic: queue lengths per iteration of the first waves (HPT_DEBUG_WAVES=n)
             --ctx->debug_waves;
             int q[MAX_ITER + 1][3];
-            CUDA_TRY(cudaStreamSynchronize(ws));
-            CUDA_TRY(cudaMemcpy(q, ctx->d_scr->qcount, sizeof(int) * 3 * (n_iter + 1), cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            CUDA_TRY(cudaMemcpy(q, scr->qcount, sizeof(int) * 3 * (n_iter + 1), cudaMemcpyDeviceToHost));
             fprintf(stderr, "wave paths=%d items=%d:", wd.n_paths, wd.n_items);
             for (int it = 0; it <= n_iter; ++it) fprintf(stderr, " [%d|%d|%d]", q[it][0], q[it][1], q[it][2]);
             fprintf(stderr, "\n");
@@ -925,6 +964,11 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
         max_depth = 1;
         return HPT_OK;
     };
+    if (two_lanes) {
+        CUDA_TRY(cudaEventRecord(ctx->ev_fork, ws));
+        CUDA_TRY(cudaStreamWaitEvent(ctx->wstream2, ctx->ev_fork, 0));
+        forked = true;
+    }
     for (int j = 0; j < n; ++j) {
         const int spp = jobs[j].spp;
         if (spp > B) return fail(HPT_ERR_UNSUPPORTED, "spp %d exceeds the wave capacity %d", spp, B);
@@ -949,7 +993,13 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
             c += take;
         }
     }
-    return flush();
+    st = flush();
+    if (st) return st;
+    if (forked) {
+        CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->wstream2));
+        CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_join, 0));
+    }
+    return HPT_OK;
 }
 
 // One launch group: the waves covering all items of 'jobs', queued on the context's wave
@@ -967,7 +1017,10 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
     CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_in, 0));
     const size_t bytes = offsetof(JobTable, jobs) + sizeof(DevJob) * n;
     CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, ws));
-    if (stats) CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
+    if (stats) {
+        CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
+        CUDA_TRY(cudaMemsetAsync(ctx->d_scr2->counters, 0, sizeof(ctx->d_scr2->counters), ws));
+    }
     st = enqueue_waves(ctx, jobs, n, prec, stats, slot->d_table, ws, true);
     if (st) return st;
     CUDA_TRY(cudaEventRecord(slot->done, ws));
@@ -1111,10 +1164,13 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
 
 static hpt_status read_status(hpt_ctx *ctx)
 {
-    unsigned bits = 0;
+    unsigned bits = 0, bits2 = 0;
     CUDA_TRY(cudaMemcpy(&bits, &ctx->d_scr->status, sizeof bits, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&bits2, &ctx->d_scr2->status, sizeof bits2, cudaMemcpyDeviceToHost));
+    bits |= bits2;
     if (bits) {
         CUDA_TRY(cudaMemset(&ctx->d_scr->status, 0, sizeof bits));
+        CUDA_TRY(cudaMemset(&ctx->d_scr2->status, 0, sizeof bits));
         return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
                     (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
     }
@@ -1145,9 +1201,10 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
     st = run_jobs(ctx, &J, 1, desc->precision, true, 0);
     if (st) return st;
     CUDA_TRY(cudaStreamSynchronize(0));
-    unsigned long long c[8];
+    unsigned long long c[8], c2[8];
     CUDA_TRY(cudaMemcpy(c, ctx->d_scr->counters, sizeof c, cudaMemcpyDeviceToHost));
-    for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k];
+    CUDA_TRY(cudaMemcpy(c2, ctx->d_scr2->counters, sizeof c2, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k] + c2[k];
     counters[0] = (uint64_t)desc->n_lambda * desc->W * (uint64_t)desc->H * desc->spp;   // path samples
     return read_status(ctx);
 }
@@ -1289,7 +1346,9 @@ static hpt_status set_capacity(hpt_ctx *ctx, int cap)
     CUDA_TRY(cudaStreamSynchronize(ctx->wstream));
     drop_graphs(ctx);
     if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
+    if (ctx->pb_arena2) CUDA_TRY(cudaFree(ctx->pb_arena2));
     ctx->pb_arena = nullptr;
+    ctx->pb_arena2 = nullptr;
     ctx->capacity = cap;
     return ensure_paths(ctx);
 }
@@ -1315,7 +1374,7 @@ extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_re
     const int old = ctx->capacity;
     size_t fr = 0, tot = 0;
     CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t avail = fr + (ctx->pb_arena ? (size_t)ctx->capacity * path_bytes() : 0);
+    const size_t avail = fr + (ctx->pb_arena ? 2 * (size_t)ctx->capacity * path_bytes() : 0);
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -1323,7 +1382,7 @@ extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_re
     double best_rate = -1.0;
     const int cands[] = {1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24};
     for (int cap : cands) {
-        if ((size_t)cap * path_bytes() > avail / 2 || cap < J.spp) continue;
+        if (2 * (size_t)cap * path_bytes() > avail / 2 || cap < J.spp) continue;
         st = set_capacity(ctx, cap);
         if (st) break;
         float best_ms = 1e30f;
