@@ -252,13 +252,14 @@ struct hpt_ctx {
     // path state of one wave (capacity paths), all wave work runs on wstream
     PathBufs pb{};
     void *pb_arena = nullptr;
-    // second wave lane: consecutive waves of a trace alternate between (pb, d_scr, wstream) and
-    // (pb2, d_scr2, wstream2), so that one wave's kernels fill the other's tails
-    void *pb_arena2 = nullptr;
-    PathBufs pb2{};
-    SlotScratch *d_scr2 = nullptr;
-    cudaStream_t wstream2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // wave lanes: consecutive waves of a trace rotate over lane 0 (pb, d_scr, wstream) and the
+    // extra lanes below, so that one wave's kernels fill the others' launch gaps and tails
+    static constexpr int EXTRA_LANES = HPT_LANES - 1;
+    void *pb_arena_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
+    PathBufs pb_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1]{};
+    SlotScratch *d_scr_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
+    cudaStream_t wstream_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
     int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
     // captured frames of hpt_trace, keyed by what fixes the launch sequence
@@ -362,11 +363,13 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
     CUDA_TRY(cudaMemset(ctx->d_scr, 0, sizeof(SlotScratch)));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream2, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-    CUDA_TRY(cudaMalloc(&ctx->d_scr2, sizeof(SlotScratch)));
-    CUDA_TRY(cudaMemset(ctx->d_scr2, 0, sizeof(SlotScratch)));
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&ctx->wstream_x[l], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join_x[l], cudaEventDisableTiming));
+        CUDA_TRY(cudaMalloc(&ctx->d_scr_x[l], sizeof(SlotScratch)));
+        CUDA_TRY(cudaMemset(ctx->d_scr_x[l], 0, sizeof(SlotScratch)));
+    }
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     // cos/sin(2 pi k / 256) split into float pairs for the double-float cone sampler
@@ -429,11 +432,13 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->pb_arena) cudaFree(ctx->pb_arena);
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     if (ctx->wstream) cudaStreamDestroy(ctx->wstream);
-    if (ctx->wstream2) cudaStreamDestroy(ctx->wstream2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-    if (ctx->pb_arena2) cudaFree(ctx->pb_arena2);
-    if (ctx->d_scr2) cudaFree(ctx->d_scr2);
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        if (ctx->wstream_x[l]) cudaStreamDestroy(ctx->wstream_x[l]);
+        if (ctx->ev_join_x[l]) cudaEventDestroy(ctx->ev_join_x[l]);
+        if (ctx->pb_arena_x[l]) cudaFree(ctx->pb_arena_x[l]);
+        if (ctx->d_scr_x[l]) cudaFree(ctx->d_scr_x[l]);
+    }
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
@@ -889,15 +894,20 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
     if (ctx->pb_arena) return HPT_OK;
     const size_t B = (size_t)ctx->capacity;
     CUDA_TRY(cudaMalloc(&ctx->pb_arena, B * path_bytes() + 64 * 256));
-    cudaError_t e = cudaMalloc(&ctx->pb_arena2, B * path_bytes() + 64 * 256);
-    if (e != cudaSuccess) {
-        cudaFree(ctx->pb_arena);
-        ctx->pb_arena = nullptr;
-        ctx->pb_arena2 = nullptr;
-        return fail(HPT_ERR_OOM, "wave state: %s", cudaGetErrorString(e));
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        cudaError_t e = cudaMalloc(&ctx->pb_arena_x[l], B * path_bytes() + 64 * 256);
+        if (e != cudaSuccess) {
+            cudaFree(ctx->pb_arena);
+            ctx->pb_arena = nullptr;
+            for (int k = 0; k < l; ++k) {
+                cudaFree(ctx->pb_arena_x[k]);
+                ctx->pb_arena_x[k] = nullptr;
+            }
+            return fail(HPT_ERR_OOM, "wave state: %s", cudaGetErrorString(e));
+        }
+        carve_paths(ctx->pb_arena_x[l], B, ctx->pb_x[l]);
     }
     carve_paths(ctx->pb_arena, B, ctx->pb);
-    carve_paths(ctx->pb_arena2, B, ctx->pb2);
     return HPT_OK;
 }
 
@@ -912,9 +922,9 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     memset(&wd, 0, sizeof wd);
     int max_depth = 1;
     hpt_status st = HPT_OK;
-    // waves alternate between two lanes (path state, scratch, stream); the second lane forks
-    // from ws at the start and joins ws at the end.  Per-kernel timing keeps one lane.
-    const bool two_lanes = ctx->timer == nullptr;
+    // waves rotate over HPT_LANES lanes (path state, scratch, stream); the extra lanes fork from
+    // ws at the start and join ws at the end.  Per-kernel timing keeps one lane.
+    const int lanes = ctx->timer == nullptr ? HPT_LANES : 1;
     int n_waves = 0;
     bool forked = false;
     auto mark = [&](int kind) -> cudaError_t {
@@ -932,11 +942,11 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     };
     auto flush = [&]() -> hpt_status {
         if (wd.n_seg == 0) return HPT_OK;
-        const int lane = two_lanes ? (n_waves & 1) : 0;
+        const int lane = n_waves % lanes;
         ++n_waves;
-        const PathBufs &pb = lane ? ctx->pb2 : ctx->pb;
-        SlotScratch *scr = lane ? ctx->d_scr2 : ctx->d_scr;
-        cudaStream_t s = lane ? ctx->wstream2 : ws;
+        const PathBufs &pb = lane ? ctx->pb_x[lane - 1] : ctx->pb;
+        SlotScratch *scr = lane ? ctx->d_scr_x[lane - 1] : ctx->d_scr;
+        cudaStream_t s = lane ? ctx->wstream_x[lane - 1] : ws;
         const int n_iter = max_depth + 1;
         CUDA_TRY(mark(HPT_K_GEN));
         CUDA_TRY(cudaMemsetAsync(scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), s));
@@ -964,9 +974,9 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
         max_depth = 1;
         return HPT_OK;
     };
-    if (two_lanes) {
+    if (lanes > 1) {
         CUDA_TRY(cudaEventRecord(ctx->ev_fork, ws));
-        CUDA_TRY(cudaStreamWaitEvent(ctx->wstream2, ctx->ev_fork, 0));
+        for (int l = 0; l < lanes - 1; ++l) CUDA_TRY(cudaStreamWaitEvent(ctx->wstream_x[l], ctx->ev_fork, 0));
         forked = true;
     }
     for (int j = 0; j < n; ++j) {
@@ -996,8 +1006,10 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     st = flush();
     if (st) return st;
     if (forked) {
-        CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->wstream2));
-        CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_join, 0));
+        for (int l = 0; l < lanes - 1; ++l) {
+            CUDA_TRY(cudaEventRecord(ctx->ev_join_x[l], ctx->wstream_x[l]));
+            CUDA_TRY(cudaStreamWaitEvent(ws, ctx->ev_join_x[l], 0));
+        }
     }
     return HPT_OK;
 }
@@ -1019,7 +1031,8 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
     CUDA_TRY(cudaMemcpyAsync(slot->d_table, h, bytes, cudaMemcpyHostToDevice, ws));
     if (stats) {
         CUDA_TRY(cudaMemsetAsync(ctx->d_scr->counters, 0, sizeof(ctx->d_scr->counters), ws));
-        CUDA_TRY(cudaMemsetAsync(ctx->d_scr2->counters, 0, sizeof(ctx->d_scr2->counters), ws));
+        for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l)
+            CUDA_TRY(cudaMemsetAsync(ctx->d_scr_x[l]->counters, 0, sizeof(ctx->d_scr->counters), ws));
     }
     st = enqueue_waves(ctx, jobs, n, prec, stats, slot->d_table, ws, true);
     if (st) return st;
@@ -1164,13 +1177,16 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
 
 static hpt_status read_status(hpt_ctx *ctx)
 {
-    unsigned bits = 0, bits2 = 0;
+    unsigned bits = 0;
     CUDA_TRY(cudaMemcpy(&bits, &ctx->d_scr->status, sizeof bits, cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(&bits2, &ctx->d_scr2->status, sizeof bits2, cudaMemcpyDeviceToHost));
-    bits |= bits2;
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        unsigned b2 = 0;
+        CUDA_TRY(cudaMemcpy(&b2, &ctx->d_scr_x[l]->status, sizeof b2, cudaMemcpyDeviceToHost));
+        bits |= b2;
+    }
     if (bits) {
         CUDA_TRY(cudaMemset(&ctx->d_scr->status, 0, sizeof bits));
-        CUDA_TRY(cudaMemset(&ctx->d_scr2->status, 0, sizeof bits));
+        for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) CUDA_TRY(cudaMemset(&ctx->d_scr_x[l]->status, 0, sizeof bits));
         return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
                     (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
     }
@@ -1201,10 +1217,13 @@ extern "C" hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const 
     st = run_jobs(ctx, &J, 1, desc->precision, true, 0);
     if (st) return st;
     CUDA_TRY(cudaStreamSynchronize(0));
-    unsigned long long c[8], c2[8];
+    unsigned long long c[8];
     CUDA_TRY(cudaMemcpy(c, ctx->d_scr->counters, sizeof c, cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(c2, ctx->d_scr2->counters, sizeof c2, cudaMemcpyDeviceToHost));
-    for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k] + c2[k];
+    for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] = c[k];
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        CUDA_TRY(cudaMemcpy(c, ctx->d_scr_x[l]->counters, sizeof c, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < HPT_NCOUNTERS; ++k) counters[k] += c[k];
+    }
     counters[0] = (uint64_t)desc->n_lambda * desc->W * (uint64_t)desc->H * desc->spp;   // path samples
     return read_status(ctx);
 }
@@ -1346,9 +1365,11 @@ static hpt_status set_capacity(hpt_ctx *ctx, int cap)
     CUDA_TRY(cudaStreamSynchronize(ctx->wstream));
     drop_graphs(ctx);
     if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
-    if (ctx->pb_arena2) CUDA_TRY(cudaFree(ctx->pb_arena2));
     ctx->pb_arena = nullptr;
-    ctx->pb_arena2 = nullptr;
+    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+        if (ctx->pb_arena_x[l]) CUDA_TRY(cudaFree(ctx->pb_arena_x[l]));
+        ctx->pb_arena_x[l] = nullptr;
+    }
     ctx->capacity = cap;
     return ensure_paths(ctx);
 }
@@ -1374,7 +1395,7 @@ extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_re
     const int old = ctx->capacity;
     size_t fr = 0, tot = 0;
     CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t avail = fr + (ctx->pb_arena ? 2 * (size_t)ctx->capacity * path_bytes() : 0);
+    const size_t avail = fr + (ctx->pb_arena ? (size_t)HPT_LANES * ctx->capacity * path_bytes() : 0);
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -1382,7 +1403,7 @@ extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_re
     double best_rate = -1.0;
     const int cands[] = {1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24};
     for (int cap : cands) {
-        if (2 * (size_t)cap * path_bytes() > avail / 2 || cap < J.spp) continue;
+        if ((size_t)HPT_LANES * cap * path_bytes() > avail / 2 || cap < J.spp) continue;
         st = set_capacity(ctx, cap);
         if (st) break;
         float best_ms = 1e30f;

@@ -6,6 +6,9 @@
 namespace hpt {
 
 constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
+#ifndef HPT_LANES
+#define HPT_LANES 3   // wave lanes of a trace (path-state sets rotating over streams)
+#endif
 #ifndef HPT_TSTACK
 #define HPT_TSTACK 32
 #endif
