@@ -260,6 +260,14 @@ struct hpt_ctx {
     SlotScratch *d_scr_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
     cudaStream_t wstream_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
     cudaEvent_t ev_fork = nullptr, ev_join_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
+    // the serving scheduler's own lanes (allocated at its first wave): its waves rotate over
+    // them independently of the trace calls' lanes
+    void *spb_arena[HPT_LANES] = {};
+    PathBufs spb[HPT_LANES]{};
+    SlotScratch *sscr[HPT_LANES] = {};
+    cudaStream_t slane_stream[HPT_LANES] = {};
+    cudaEvent_t slane_ev[HPT_LANES] = {};   // end of the lane's latest wave
+    int sched_next = 0;
     int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
     int debug_waves = 0;
     // captured frames of hpt_trace, keyed by what fixes the launch sequence
@@ -320,7 +328,6 @@ struct hpt_ctx {
     size_t rr = 0;
     bool stop = false;
     std::thread sched;
-    cudaStream_t sstream = nullptr;
     double now_us() const
     {
         return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
@@ -397,7 +404,6 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
         CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         ctx->budget = (uint64_t)(fr * 0.6);
     }
-    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking));
     hpt_ctx *raw = ctx.release();
     raw->sched = std::thread(sched_loop, raw);
     *out = raw;
@@ -433,6 +439,12 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     if (ctx->wstream) cudaStreamDestroy(ctx->wstream);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    for (int l = 0; l < HPT_LANES; ++l) {
+        if (ctx->slane_stream[l]) cudaStreamDestroy(ctx->slane_stream[l]);
+        if (ctx->slane_ev[l]) cudaEventDestroy(ctx->slane_ev[l]);
+        if (ctx->spb_arena[l]) cudaFree(ctx->spb_arena[l]);
+        if (ctx->sscr[l]) cudaFree(ctx->sscr[l]);
+    }
     for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
         if (ctx->wstream_x[l]) cudaStreamDestroy(ctx->wstream_x[l]);
         if (ctx->ev_join_x[l]) cudaEventDestroy(ctx->ev_join_x[l]);
@@ -443,7 +455,6 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
     if (ctx->d_sincos) cudaFree(ctx->d_sincos);
-    if (ctx->sstream) cudaStreamDestroy(ctx->sstream);
     delete ctx;
 }
 
@@ -911,6 +922,31 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
     return HPT_OK;
 }
 
+// the serving scheduler's lanes; caller holds ctx->mu
+static hpt_status ensure_sched_paths(hpt_ctx *ctx)
+{
+    if (ctx->spb_arena[0]) return HPT_OK;
+    const size_t B = (size_t)ctx->capacity;
+    for (int l = 0; l < HPT_LANES; ++l) {
+        if (!ctx->slane_stream[l]) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->slane_stream[l], cudaStreamNonBlocking));
+        if (!ctx->slane_ev[l]) CUDA_TRY(cudaEventCreateWithFlags(&ctx->slane_ev[l], cudaEventDisableTiming));
+        if (!ctx->sscr[l]) {
+            CUDA_TRY(cudaMalloc(&ctx->sscr[l], sizeof(SlotScratch)));
+            CUDA_TRY(cudaMemset(ctx->sscr[l], 0, sizeof(SlotScratch)));
+        }
+        cudaError_t e = cudaMalloc(&ctx->spb_arena[l], B * path_bytes() + 64 * 256);
+        if (e != cudaSuccess) {
+            for (int k = 0; k <= l; ++k) {
+                if (ctx->spb_arena[k]) cudaFree(ctx->spb_arena[k]);
+                ctx->spb_arena[k] = nullptr;
+            }
+            return fail(HPT_ERR_OOM, "serving wave state: %s", cudaGetErrorString(e));
+        }
+        carve_paths(ctx->spb_arena[l], B, ctx->spb[l]);
+    }
+    return HPT_OK;
+}
+
 // One launch group: the waves covering all items of 'jobs', queued on the context's wave
 // stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
 // Queue the waves that cover all items of 'jobs' (job table already on the device) on ws.
@@ -1184,6 +1220,13 @@ static hpt_status read_status(hpt_ctx *ctx)
         CUDA_TRY(cudaMemcpy(&b2, &ctx->d_scr_x[l]->status, sizeof b2, cudaMemcpyDeviceToHost));
         bits |= b2;
     }
+    for (int l = 0; l < HPT_LANES; ++l) {
+        if (!ctx->sscr[l]) continue;
+        unsigned b2 = 0;
+        CUDA_TRY(cudaMemcpy(&b2, &ctx->sscr[l]->status, sizeof b2, cudaMemcpyDeviceToHost));
+        if (b2) CUDA_TRY(cudaMemset(&ctx->sscr[l]->status, 0, sizeof b2));
+        bits |= b2;
+    }
     if (bits) {
         CUDA_TRY(cudaMemset(&ctx->d_scr->status, 0, sizeof bits));
         for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) CUDA_TRY(cudaMemset(&ctx->d_scr_x[l]->status, 0, sizeof bits));
@@ -1364,11 +1407,16 @@ static hpt_status set_capacity(hpt_ctx *ctx, int cap)
     if (cap == ctx->capacity && ctx->pb_arena) return HPT_OK;
     CUDA_TRY(cudaStreamSynchronize(ctx->wstream));
     drop_graphs(ctx);
+    CUDA_TRY(cudaDeviceSynchronize());
     if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
     ctx->pb_arena = nullptr;
     for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
         if (ctx->pb_arena_x[l]) CUDA_TRY(cudaFree(ctx->pb_arena_x[l]));
         ctx->pb_arena_x[l] = nullptr;
+    }
+    for (int l = 0; l < HPT_LANES; ++l) {
+        if (ctx->spb_arena[l]) CUDA_TRY(cudaFree(ctx->spb_arena[l]));
+        ctx->spb_arena[l] = nullptr;
     }
     ctx->capacity = cap;
     return ensure_paths(ctx);
@@ -1530,7 +1578,7 @@ static void sched_loop(hpt_ctx *ctx)
             InflightWave w;
             {
                 std::lock_guard<std::mutex> lk(ctx->mu);
-                st = ensure_paths(ctx);
+                st = ensure_sched_paths(ctx);
                 Slot *slot = st ? nullptr : acquire_slot(ctx);
                 WaveDesc wd;
                 memset(&wd, 0, sizeof wd);
@@ -1552,17 +1600,21 @@ static void sched_loop(hpt_ctx *ctx)
                         wd.n_items += pk.second;
                         max_depth = std::max(max_depth, r.job.max_depth);
                     }
-                    cudaStream_t ws = ctx->wstream;
+                    // this wave's lane: path state, scratch and stream of its own
+                    const int lane = ctx->sched_next++ % HPT_LANES;
+                    cudaStream_t ws = ctx->slane_stream[lane];
+                    const PathBufs &lpb = ctx->spb[lane];
+                    SlotScratch *lscr = ctx->sscr[lane];
                     const int n_iter = max_depth + 1;
                     bool ok = cudaMemcpyAsync(slot->d_table, h, offsetof(JobTable, jobs) + sizeof(DevJob) * h->n_jobs,
                                               cudaMemcpyHostToDevice, ws) == cudaSuccess;
-                    ok = ok && cudaMemsetAsync(ctx->d_scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws) == cudaSuccess;
-                    ok = ok && wave_gen(prec, slot->d_table, wd, ctx->pb, ctx->d_scr, ws) == cudaSuccess;
+                    ok = ok && cudaMemsetAsync(lscr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws) == cudaSuccess;
+                    ok = ok && wave_gen(prec, slot->d_table, wd, lpb, lscr, ws) == cudaSuccess;
                     for (int it = 0; ok && it < n_iter; ++it) {
-                        ok = wave_trace(prec, false, slot->d_table, wd, ctx->pb, ctx->d_scr, it, ctx->grid_trace[prec], ws) == cudaSuccess;
-                        ok = ok && wave_shade(prec, false, slot->d_table, wd, ctx->pb, ctx->d_scr, it, ctx->grid_shade[prec], ws) == cudaSuccess;
+                        ok = wave_trace(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_trace[prec], ws) == cudaSuccess;
+                        ok = ok && wave_shade(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_shade[prec], ws) == cudaSuccess;
                     }
-                    ok = ok && wave_accum(prec, slot->d_table, wd, ctx->pb, ctx->d_scr, ws) == cudaSuccess;
+                    ok = ok && wave_accum(prec, slot->d_table, wd, lpb, lscr, ws) == cudaSuccess;
                     ok = ok && cudaEventRecord(slot->done, ws) == cudaSuccess;
                     {
                         std::lock_guard<std::mutex> lk2(ctx->smu);
@@ -1572,7 +1624,13 @@ static void sched_loop(hpt_ctx *ctx)
                         }
                     }
                     if (!w.ev) cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
+                    // the wave's event also covers the waves issued before it on the other lanes,
+                    // so that a request counts as done only when all its waves are (the waits
+                    // follow this wave's kernels and hold back nothing but the event)
+                    for (int l = 0; ok && l < HPT_LANES; ++l)
+                        if (l != lane) ok = cudaStreamWaitEvent(ws, ctx->slane_ev[l], 0) == cudaSuccess;
                     ok = ok && cudaEventRecord(w.ev, ws) == cudaSuccess;
+                    ok = ok && cudaEventRecord(ctx->slane_ev[lane], ws) == cudaSuccess;
                     if (!ok) st = HPT_ERR_CUDA;
                 }
             }
@@ -1590,13 +1648,13 @@ static void sched_loop(hpt_ctx *ctx)
             }
             (void)st;
         }
-        // keep at most two waves queued ahead; retire finished ones
+        // keep at most one wave per lane queued ahead; retire finished ones
         size_t nin;
         {
             std::lock_guard<std::mutex> lk(ctx->smu);
             nin = ctx->inflight.size();
         }
-        if (nin > 2 || (picks.empty() && (idle_wait || nin > 0))) retire_oldest(ctx);
+        if (nin > HPT_LANES || (picks.empty() && (idle_wait || nin > 0))) retire_oldest(ctx);
     }
     // shutting down: nothing left in flight; pending requests are dropped
 }
