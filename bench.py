@@ -193,10 +193,30 @@ def cpu_oracle_rate(scene, r, n_pixels, seed=5):
     pix = rng.choice(r.W * r.H, n_pixels, replace=False)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    o.trace(r, pix, n_threads=cores)
+    U = o.trace(r, pix, n_threads=cores)
     dt = time.perf_counter() - t0
     samples = n_pixels * len(r.lambdas) * r.spp
-    return samples / dt, dt, cores, samples
+    return samples / dt, dt, cores, samples, pix, U
+
+
+def precision_report(U, ref):
+    """Error of GPU fields U[lambda][m][pixel] against the FP64 oracle's ref, per output: the
+    fraction of pixels within 1e-4 relative error and 1e-3 rad (where |ref| < 1e-3 RMS the bound
+    is 1e-4 RMS; the phase is checked where |ref| >= 0.1 RMS), the median and maximum relative
+    error and the maximum phase error."""
+    out = []
+    for l in range(U.shape[0]):
+        for m in range(U.shape[1]):
+            u, q = np.asarray(U[l, m], np.complex128), np.asarray(ref[l, m], np.complex128)
+            rms = float(np.sqrt(np.mean(np.abs(q) ** 2)))
+            a, d = np.abs(q), np.abs(u - q)
+            rel = np.where(a < 1e-3 * rms, d / max(rms, 1e-300), d / np.maximum(a, 1e-300))
+            ph = np.where(a >= 0.1 * rms, np.abs(np.angle(u * np.conj(q))), 0.0)
+            ok = (rel <= 1e-4) & (ph <= 1e-3)
+            out.append({"lambda": l, "m": m, "pass_frac": float(ok.mean()), "median_rel": float(np.median(rel)),
+                        "max_rel": float(rel.max()), "max_phase_rad": float(ph.max())})
+    return {"outputs": out, "min_pass_frac": min(x["pass_frac"] for x in out),
+            "max_phase_rad": max(x["max_phase_rad"] for x in out), "pixels": int(U.shape[2])}
 
 
 def _pose_T(dx, dy, dz):
@@ -340,10 +360,10 @@ def run_reference(args):
     r = getattr(S, render_fn)(**wl_over)
     n_pix = 2048 if args.workload != "cfg3" else 256
     for _ in range(args.warmup):
-        cpu_oracle_rate(sc, r, max(n_pix // 8, 16))
+        cpu_oracle_rate(sc, r, max(n_pix // 8, 16))[0]
     rates, dts, samples = [], [], 0
     for k in range(args.steps):
-        rate, dt, cores, ns = cpu_oracle_rate(sc, r, n_pix, seed=100 + k)
+        rate, dt, cores, ns = cpu_oracle_rate(sc, r, n_pix, seed=100 + k)[:4]
         dts.append(dt)
         samples += ns
     total = sum(dts)
@@ -501,9 +521,28 @@ def main():
         ctx.sync()
 
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         npx = 8192 if args.workload != "cfg3" else 1024
-        rate, dt, cores, nsamp = cpu_oracle_rate(sc, r, npx)
+        # the fields of both forms, traced once more outside the timing (later measurements reuse
+        # the buffers), for the error report against the oracle's pixels
+        ctx.trace(sid, r, out, precision=hpt.PREC_DF32, stream=stream)
+        if not args.no_plain:
+            step_plain()
+        ctx.sync()
+        torch.cuda.synchronize()
+        rate, dt, cores, nsamp, pix, ref = cpu_oracle_rate(sc, r, npx)
+        pix_t = torch.from_numpy(np.asarray(pix)).to(out.device)
+        U_df = out.reshape(out.shape[0], out.shape[1], -1)[:, :, pix_t].cpu().numpy()
+        precision = {"df32": precision_report(U_df, ref)}
+        if not args.no_plain:
+            # the plain form renders each wavelength on its own (wavelength index 0 in the draws):
+            # its reference is the oracle on those single-wavelength renders
+            import oracle
+            orc = oracle.Oracle(sc)
+            U_64 = np.stack([o.reshape(o.shape[1], -1)[:, pix_t].cpu().numpy() for o in outs_plain])
+            ref_64 = np.concatenate([orc.trace(rp, np.asarray(pix)) for rp in r_plain])
+            precision["fp64"] = precision_report(U_64, ref_64)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{npx} seeded random pixels of the {r.W}x{r.H} frame x {len(r.lambdas)} wavelengths x "
                          f"{r.spp} spp ({nsamp} path samples, {dt:.1f} s)"}
@@ -519,7 +558,7 @@ def main():
                 "idle_ms_per_step": (total_ms - sum(launch_ms)) / args.steps,
                 "gaps_ms": [round(g, 3) for g in gaps_ms[0]],
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * sum(n for _, n in kt.values()),
-                "graph_launches": args.steps, "roofline": roofline, "optics": optics, "serving": serving,
+                "graph_launches": args.steps, "roofline": roofline, "optics": optics, "serving": serving, "precision": precision,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
