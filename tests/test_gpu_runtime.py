@@ -108,3 +108,34 @@ def test_timed_trace_reports_kernels_and_keeps_results(torch_cuda):
         assert all(ms > 0 for ms, _ in t.values())
     finally:
         ctx.close()
+
+
+def test_many_waves_over_lanes_graph_and_direct(torch_cuda, oracle_mod):
+    """A frame split into many small waves (65536 paths each) rotates over the wave lanes, in a
+    captured graph and in direct launches: the two agree bit for bit and match the oracle."""
+    import os
+    from paper_2606_14173_gb300 import hpt
+    from tests.parity import assert_parity
+    old = os.environ.get("HPT_WAVE_PATHS")
+    os.environ["HPT_WAVE_PATHS"] = "65536"
+    try:
+        direct = hpt.Context(0, graphs=False)
+        graphed = hpt.Context(0, graphs=True)
+    finally:
+        if old is None:
+            del os.environ["HPT_WAVE_PATHS"]
+        else:
+            os.environ["HPT_WAVE_PATHS"] = old
+    try:
+        sc = S.config1_scene()
+        sd, sg = direct.upload_scene(sc), graphed.upload_scene(sc)
+        r = S.config1_render(W=160, H=96, spp=8, K=2)        # 368640 paths: 6 waves
+        od, og = hpt.alloc_output(r), hpt.alloc_output(r)
+        a = _trace(direct, sd, r, od)
+        for _ in range(2):                                    # capture, then replay
+            b = _trace(graphed, sg, r, og)
+            assert np.array_equal(a, b)
+        assert_parity(a, oracle_mod.Oracle(sc).trace_full(r), "many waves")
+    finally:
+        direct.close()
+        graphed.close()
