@@ -499,8 +499,11 @@ def main():
     achieved = trace_flops / (trace_ms / 1e3) / 1e12
     kern_total = sum(ms for ms, _ in kt.values())
     traffic = TRACE_DRAM_BYTES_PER_LAUNCH if args.workload in ("cfg2", "band") else None
+    probes = ctx.probe_peaks() if not args.no_counters else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_trace",
+                "measured_probes": probes,
+                "frac_of_measured_fp32": (achieved / probes["fp32_tflops"]) if probes else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
                 "launches_per_frame": trace_launches, "ms_per_launch": trace_ms / max(trace_launches, 1),
                 "flop_per_launch": trace_flops / max(trace_launches, 1),

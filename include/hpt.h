@@ -256,6 +256,14 @@ hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, float *phi_dev
                             double lambda, double pitch, double z, int32_t iters, float lr, double *losses,
                             void *stream);
 
+/* ---- probes ---------------------------------------------------------------------------- */
+/* Measured throughputs of this device for the roofline (the paper has no counterpart):
+ * peaks[0] FP32 FMA TFLOP/s, peaks[1] FP64 FMA TFLOP/s (2 flops per FMA, eight independent
+ * chains per thread, 8 blocks of 256 threads per SM), peaks[2] L2 read GB/s over a 64 MiB
+ * buffer, peaks[3] the SM count.  Synchronous; allocates and frees 64 MiB. */
+enum { HPT_NPEAKS = 4 };
+hpt_status hpt_probe_peaks(hpt_ctx *ctx, double peaks[HPT_NPEAKS]);
+
 /* ---- ambient cache construction (texture baking, Sec. 4.4) ---------------------------- */
 /* The supplementary section that defines the bake is not available; this is the reading.
  * For cell (ix, iy, iz) of a res^3 grid over [bmin, bmax] (centre x = bmin + (i + 0.5)

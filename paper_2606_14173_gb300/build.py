@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libhpt.so")
-SOURCES = ["hpt_host.cu", "hpt_kernel.cu", "hpt_wave_f64.cu", "hpt_wave_df.cu", "hpt_static.cu", "hpt_optics.cu"]
+SOURCES = ["hpt_host.cu", "hpt_kernel.cu", "hpt_wave_f64.cu", "hpt_wave_df.cu", "hpt_static.cu", "hpt_optics.cu", "hpt_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

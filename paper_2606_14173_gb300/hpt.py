@@ -25,7 +25,8 @@ COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_f
 SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "hpt_scene_release", "hpt_scene_info",
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
            "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
-           "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache", "hpt_phase_encode"]
+           "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache", "hpt_phase_encode",
+           "hpt_probe_peaks"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_trace_host.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
+    lib.hpt_probe_peaks.argtypes = [vp, C.POINTER(C.c_double)]
     lib.hpt_phase_encode.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                                      C.c_float, C.POINTER(C.c_double), vp]
     lib.hpt_cache_bake.argtypes = [vp, C.c_uint64, C.POINTER(BakeDesc), vp, C.c_size_t, vp]
@@ -263,6 +265,12 @@ class Context:
         n = (C.c_uint32 * len(KERNEL_NAMES))()
         _check(self.lib.hpt_trace_timed(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(ptr), nbytes, ms, n))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def probe_peaks(self):
+        """Measured FP32 / FP64 FMA TFLOP/s, L2 read GB/s and the SM count of this device."""
+        p = (C.c_double * 4)()
+        _check(self.lib.hpt_probe_peaks(self.h, p))
+        return {"fp32_tflops": p[0], "fp64_tflops": p[1], "l2_read_gbs": p[2], "sms": int(p[3])}
 
     def phase_encode(self, target, phi, lam: float, pitch: float, z: float, iters: int, lr: float, stream=None):
         """Gradient steps on phi (float32 CUDA tensor [H][W], updated in place) towards the complex

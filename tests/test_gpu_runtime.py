@@ -139,3 +139,15 @@ def test_many_waves_over_lanes_graph_and_direct(torch_cuda, oracle_mod):
     finally:
         direct.close()
         graphed.close()
+
+
+def test_probe_peaks_are_plausible(torch_cuda):
+    from paper_2606_14173_gb300 import hpt
+    ctx = hpt.Context(0)
+    try:
+        p = ctx.probe_peaks()
+        assert p["sms"] >= 1
+        assert p["fp32_tflops"] > 1.0 and p["fp64_tflops"] > 0.01 and p["l2_read_gbs"] > 100.0
+        assert p["fp64_tflops"] < p["fp32_tflops"]
+    finally:
+        ctx.close()
