@@ -137,7 +137,9 @@ typedef struct {
  *  precision     HPT_PREC_FP64 or HPT_PREC_DF32 (coherent chain arithmetic)
  *  use_cache     read the scene's ambient cache past the first incoherent bounce
  *  grf_phi       HPT_PHASE_GRF only: device pointer, float radians [K][grf_ny][grf_nx],
- *                caller-owned, must stay valid until the trace completes; else NULL    */
+ *                caller-owned, must stay valid until the trace completes; else NULL
+ *  omit_obliquity 0: the obliquity factor cos(theta) of Eq. 2 is applied (default);
+ *                1: left out (a point emitter then gives exactly a exp(ikr) / r)           */
 typedef struct {
     int32_t W, H;
     double pitch;
@@ -153,6 +155,7 @@ typedef struct {
     int32_t use_cache;
     const float *grf_phi;
     int32_t grf_nx, grf_ny;
+    int32_t omit_obliquity;
 } hpt_render_desc;
 
 /* Output layout of every trace: complex64 (float re, float im) [n_lambda][K][H][W];
@@ -284,6 +287,11 @@ typedef struct {
 } hpt_bake_desc;
 hpt_status hpt_cache_bake(hpt_ctx *ctx, uint64_t scene_id, const hpt_bake_desc *desc, float *E_dev,
                           size_t E_bytes, void *stream);
+/* Upload an ambient cache from host memory: binary16 [res][res][res][3] ([z][y][x][c], IEEE
+ * bits) over [bmin, bmax]; the library copies it (res = 0 removes the cache).  Synchronises
+ * the device first; HPT_ERR_BUSY while queued requests use the scene. */
+hpt_status hpt_cache_upload(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
+                            const float bmax[3], const uint16_t *E_half_host);
 /* Replace the scene's ambient cache by the float grid E_dev [res][res][res][3] over [bmin,
  * bmax] (device memory, converted to binary16 with round to nearest even; res = 0 removes
  * the cache).  Synchronises the device first (traces in flight may read the old cache);

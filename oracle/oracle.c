@@ -909,7 +909,7 @@ static int coherent_sample(ctx_t *C, samp_t *out)
             out->cos_p = cos_p;
             /* RS estimator (Eq. 2) with the area-measure pdf of the sampled point */
             double pdf_A = pdf_w * cos_p / (rr * rr);
-            out->base = out->A * cos_t / (rr * pdf_A * lambda);
+            out->base = out->A * (r->omit_obliquity ? 1.0 : cos_t) / (rr * pdf_A * lambda);
             out->sens = 0.0;
             if (cond) {
                 double g = sqrt(beta) * fabs(cos_t) / (rr * pdf_A * lambda);
@@ -988,7 +988,7 @@ static void point_field(ctx_t *C, double *re, double *im)
         int64_t nf = 0;
         if (occluded(o, O, scl(dw, 1.0 / dist), dist * (1.0 - SHADOW_SHRINK), -1, &nf)) continue;
         double turns = fmod(rr / lambda, 1.0);
-        double a = pe[3] * ct / rr;
+        double a = pe[3] * (r->omit_obliquity ? 1.0 : ct) / rr;
         *re += a * cos(2.0 * PI * turns);
         *im += a * sin(2.0 * PI * turns);
     }

@@ -57,6 +57,7 @@ typedef struct {
     int32_t use_cache;
     int32_t grf_nx, grf_ny;  /* phase_mode 2: periodic GRF phase grid (pitch = the SLM pitch) */
     const double *grf_phi;   /* [K][grf_ny][grf_nx] radians, hologram_offset + m for map m */
+    int32_t omit_obliquity;  /* 1: leave out the cos(theta) factor of Eq. 2 */
 } or_render;
 
 /* per-sample debug record (or_sample) */

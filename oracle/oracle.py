@@ -50,7 +50,7 @@ class OrRender(C.Structure):
                 ("max_depth", C.c_int32), ("K", C.c_int32), ("hologram_offset", C.c_int32),
                 ("seed", C.c_uint64), ("phase_seed", C.c_uint64), ("phase_mode", C.c_int32),
                 ("facet_size", C.c_double), ("T", C.c_double * 16), ("use_cache", C.c_int32),
-                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("grf_phi", C.c_void_p)]
+                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("grf_phi", C.c_void_p), ("omit_obliquity", C.c_int32)]
 
 
 class OrBake(C.Structure):
@@ -118,6 +118,7 @@ def _render_struct(r, grf=None) -> OrRender:
     for i in range(16):
         s.T[i] = float(T[i])
     s.use_cache = int(r.use_cache)
+    s.omit_obliquity = int(getattr(r, "omit_obliquity", 0))
     if grf is not None:
         assert grf.dtype == np.float64 and grf.flags.c_contiguous and grf.ndim == 3 and grf.shape[0] >= r.K
         s.grf_ny, s.grf_nx = int(grf.shape[1]), int(grf.shape[2])

@@ -810,6 +810,7 @@ static hpt_status make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
     J.grf_nx = r->phase_mode == HPT_PHASE_GRF ? r->grf_nx : 0;
     J.grf_ny = r->phase_mode == HPT_PHASE_GRF ? r->grf_ny : 0;
     J.use_cache = r->use_cache ? 1 : 0;
+    J.obliquity = r->omit_obliquity ? 0 : 1;
     J.n_tiles_x = (r->W + TILE_W - 1) / TILE_W;
     J.n_tiles = J.n_tiles_x * ((r->H + TILE_H - 1) / TILE_H);
     J.n_items = (long long)r->n_lambda * J.n_tiles * 32;
@@ -1360,14 +1361,15 @@ extern "C" hpt_status hpt_cache_bake(hpt_ctx *ctx, uint64_t scene_id, const hpt_
     return run_jobs(ctx, &J, 1, HPT_PREC_DF32, false, (cudaStream_t)stream);
 }
 
-extern "C" hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
-                                          const float bmax[3], const float *E_dev)
+// replace the cache from a device float grid (E_dev) or a host binary16 grid (E_half)
+static hpt_status set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3], const float bmax[3],
+                            const float *E_dev, const uint16_t *E_half)
 {
-    g_err.clear();
-    hpt_status st = check_ctx(ctx);
-    if (st) return st;
-    if (!bmin || !bmax || (res > 0 && !E_dev)) return fail(HPT_ERR_INVALID_ARG, "bmin, bmax or E_dev is NULL");
+    if (!bmin || !bmax || (res > 0 && !E_dev && !E_half)) return fail(HPT_ERR_INVALID_ARG, "bmin, bmax or the grid is NULL");
     if (res < 0 || res > 1024) return fail(HPT_ERR_INVALID_ARG, "res must be 0..1024");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(bmin[k]) || !std::isfinite(bmax[k]) || !(bmax[k] > bmin[k]))
+            return fail(HPT_ERR_INVALID_ARG, "need finite bmin < bmax");
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto it = ctx->scenes.find(scene_id);
     if (it == ctx->scenes.end()) return fail(HPT_ERR_NOT_FOUND, "unknown scene %llu", (unsigned long long)scene_id);
@@ -1382,8 +1384,12 @@ extern "C" hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32
     if (res > 0) {
         const size_t n = (size_t)res * res * res * 3;
         CUDA_TRY(cudaMalloc(&rec->cache_buf, n * sizeof(unsigned short)));
-        k_to_half<<<(int)std::min<size_t>((n + 255) / 256, 152 * 32), 256>>>(E_dev, (unsigned short *)rec->cache_buf, n);
-        CUDA_TRY(cudaGetLastError());
+        if (E_dev) {
+            k_to_half<<<(int)std::min<size_t>((n + 255) / 256, 152 * 32), 256>>>(E_dev, (unsigned short *)rec->cache_buf, n);
+            CUDA_TRY(cudaGetLastError());
+        } else {
+            CUDA_TRY(cudaMemcpy(rec->cache_buf, E_half, n * sizeof(unsigned short), cudaMemcpyHostToDevice));
+        }
         CUDA_TRY(cudaDeviceSynchronize());
         rec->dev.cache = (const unsigned short *)rec->cache_buf;
     }
@@ -1394,6 +1400,25 @@ extern "C" hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32
     }
     return HPT_OK;
 }
+
+extern "C" hpt_status hpt_cache_upload(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
+                                       const float bmax[3], const uint16_t *E_half_host)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    return set_cache(ctx, scene_id, res, bmin, bmax, nullptr, E_half_host);
+}
+
+extern "C" hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, const float bmin[3],
+                                          const float bmax[3], const float *E_dev)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    return set_cache(ctx, scene_id, res, bmin, bmax, E_dev, nullptr);
+}
+
 
 // ---------------------------------------------------------------------------- autotune
 static void drop_graphs(hpt_ctx *ctx)

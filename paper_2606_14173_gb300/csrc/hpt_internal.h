@@ -98,6 +98,7 @@ struct DevJob {
     // kind 1: ambient-cache bake; items are (channel, cell) with the cells laid out as a
     // W = res by H = res^2 image, each path an incoherent ray from the cell centre
     int kind;
+    int obliquity;              // 1: cos(theta) of Eq. 2 applied, 0: omitted
     float *bake_out;            // [res^3][3] float
     float bake_lo[3], bake_h[3];
 };

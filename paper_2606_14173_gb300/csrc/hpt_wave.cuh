@@ -543,7 +543,9 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                         pb.cy[p] = RO::floor_i(P.y * ih);
                         pb.cz[p] = RO::floor_i(P.z * ih);
                     }
-                    pb.basep[p] = pb.cost[p] * RO::to_f(opl) / (J.pdf_w[id.lam] * cosP * J.lambda_f[id.lam]);
+                    // Eq. 2 with the obliquity factor cos(theta) (unless omitted)
+                    pb.basep[p] = (J.obliquity ? pb.cost[p] : 1.0f) * RO::to_f(opl) /
+                                  (J.pdf_w[id.lam] * cosP * J.lambda_f[id.lam]);
                     // the incoherent part starts at P: handed to this iteration's incoherent
                     // shading as a hit at distance 0 from P (vertex count cv after its increment),
                     // so that the coherent kernel carries no BSDF / NEE code
@@ -717,7 +719,7 @@ __device__ __noinline__ float2 point_field(const DevJob *Jp, int lam, int px, in
         const float turns = RO::frac_f(r * RO::rc(J.inv_lambda[lam]));
         float sn, cs;
         sincospif(2.0f * turns, &sn, &cs);
-        const float a = (float)pe[3] * ct / rf;
+        const float a = (float)pe[3] * (J.obliquity ? ct : 1.0f) / rf;
         acc.x += a * cs;
         acc.y += a * sn;
     }

@@ -26,7 +26,7 @@ SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "h
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
            "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
            "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache", "hpt_phase_encode",
-           "hpt_probe_peaks"]
+           "hpt_probe_peaks", "hpt_cache_upload"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -63,7 +63,7 @@ class RenderDesc(C.Structure):
                 ("K", C.c_int32), ("hologram_offset", C.c_int32), ("seed", C.c_uint64), ("phase_seed", C.c_uint64),
                 ("phase_mode", C.c_int32), ("facet_size", C.c_double), ("T", C.c_double * 16),
                 ("precision", C.c_int32), ("use_cache", C.c_int32), ("grf_phi", C.c_void_p),
-                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32)]
+                ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("omit_obliquity", C.c_int32)]
 
 
 class BakeDesc(C.Structure):
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_sync.argtypes = [vp]
     lib.hpt_trace_counters.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, C.POINTER(C.c_uint64)]
     lib.hpt_probe_peaks.argtypes = [vp, C.POINTER(C.c_double)]
+    lib.hpt_cache_upload.argtypes = [vp, C.c_uint64, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), vp]
     lib.hpt_phase_encode.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                                      C.c_float, C.POINTER(C.c_double), vp]
     lib.hpt_cache_bake.argtypes = [vp, C.c_uint64, C.POINTER(BakeDesc), vp, C.c_size_t, vp]
@@ -138,6 +139,7 @@ def render_desc(r, precision=PREC_DF32) -> RenderDesc:
         d.T[i] = float(T[i])
     d.precision = int(precision)
     d.use_cache = int(r.use_cache)
+    d.omit_obliquity = int(getattr(r, "omit_obliquity", 0))
     g = getattr(r, "grf", None)
     if g is not None:
         if not (g.is_cuda and g.dtype.is_floating_point and g.element_size() == 4 and g.is_contiguous()
@@ -299,6 +301,16 @@ class Context:
         _check(self.lib.hpt_cache_bake(self.h, C.c_uint64(sid), C.byref(d), C.c_void_p(E.data_ptr()),
                                        E.numel() * 4, _stream_ptr(stream)))
         return E
+
+    def cache_upload(self, sid: int, E_half, bmin, bmax):
+        """Upload a host binary16 cache [res][res][res][3] (numpy float16) to the scene."""
+        E_half = np.ascontiguousarray(E_half, np.float16)
+        if not (E_half.ndim == 4 and E_half.shape[0] == E_half.shape[1] == E_half.shape[2] and E_half.shape[3] == 3):
+            raise ValueError("E_half must be [res][res][res][3]")
+        lo = (C.c_float * 3)(*[float(x) for x in bmin])
+        hi = (C.c_float * 3)(*[float(x) for x in bmax])
+        _check(self.lib.hpt_cache_upload(self.h, C.c_uint64(sid), int(E_half.shape[0]), lo, hi,
+                                         C.c_void_p(E_half.ctypes.data)))
 
     def set_cache(self, sid: int, E, bmin, bmax):
         """Replace the scene's ambient cache by the float32 CUDA tensor E [res][res][res][3] (None: remove)."""

@@ -107,6 +107,7 @@ class Render:
     T: np.ndarray = field(default_factory=lambda: np.eye(4))  # world -> hologram
     use_cache: int = 0
     grf: object = None                 # phase mode 2: device phase maps [K][ny][nx] (float32 radians)
+    omit_obliquity: int = 0            # 1: leave out the cos(theta) factor of Eq. 2
 
     @property
     def n_lambda(self) -> int:

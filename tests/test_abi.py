@@ -48,6 +48,7 @@ int main(void) {
   printf("%zu %zu %zu %d\n", offsetof(hpt_render_desc, grf_phi), offsetof(hpt_render_desc, grf_nx),
          offsetof(hpt_render_desc, grf_ny), HPT_PHASE_GRF);
   printf("%zu %zu %zu\n", sizeof(hpt_bake_desc), offsetof(hpt_bake_desc, spp), offsetof(hpt_bake_desc, seed));
+  printf("%zu\n", offsetof(hpt_render_desc, omit_obliquity));
   return 0;
 }
 '''
@@ -64,7 +65,8 @@ int main(void) {
            hpt.RenderDesc.use_cache.offset, hpt.NCOUNTERS, len(hpt.KERNEL_NAMES),
            hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum"),
            hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF,
-           C.sizeof(hpt.BakeDesc), hpt.BakeDesc.spp.offset, hpt.BakeDesc.seed.offset]
+           C.sizeof(hpt.BakeDesc), hpt.BakeDesc.spp.offset, hpt.BakeDesc.seed.offset,
+           hpt.RenderDesc.omit_obliquity.offset]
     assert [int(x) for x in out] == got
 
 

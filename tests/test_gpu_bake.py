@@ -120,3 +120,25 @@ def test_bake_invalid_arguments(ctx, torch_cuda):
         ctx.cache_bake(sid + 1000, 4, [0, 0, 0], [1, 1, 1], 4, 2)
     ctx.sync()
     ctx.release_scene(sid)
+
+
+def test_cache_upload_from_host_equals_device_set(ctx, torch_cuda):
+    """The same binary16 grid uploaded from host memory and set from a device float grid (whose
+    values are exactly representable in binary16) gives the same traced fields bit for bit."""
+    torch = torch_cuda
+    from paper_2606_14173_gb300 import hpt
+    base = S.config1_scene()
+    a_sid, b_sid = ctx.upload_scene(base), ctx.upload_scene(base)
+    res = 16
+    lo, hi = [-20 * MM, -3 * MM, 0.0], [20 * MM, 15 * MM, 40 * MM]
+    grid16 = np.random.default_rng(9).uniform(0.5, 3.0, (res, res, res, 3)).astype(np.float16)
+    ctx.cache_upload(a_sid, grid16, lo, hi)
+    ctx.set_cache(b_sid, torch.from_numpy(grid16.astype(np.float32)).cuda(), lo, hi)
+    r = S.config1_render(W=96, H=64, spp=8, K=1, use_cache=1)
+    oa, ob = hpt.alloc_output(r), hpt.alloc_output(r)
+    ctx.trace(a_sid, r, oa)
+    ctx.trace(b_sid, r, ob)
+    ctx.sync()
+    assert torch.equal(oa, ob)
+    ctx.release_scene(a_sid)
+    ctx.release_scene(b_sid)

@@ -218,3 +218,11 @@ def test_config3_full_size_sampled(ctx, cfg3):
     assert_parity_explained(U.reshape(3, 8, -1)[:, :, pix], ref, flags, sens, "cfg3 sampled")
     info = ctx.scene_info(sid)
     assert info["depth"] <= 31
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_without_obliquity(ctx, cfg1, prec):
+    """The obliquity factor of Eq. 2 left out: the fields still follow the oracle."""
+    sc, sid, orc = cfg1
+    r = S.config1_render(W=131, H=77, spp=8, K=2, omit_obliquity=1)
+    assert_parity(gpu_trace(ctx, sid, r, prec), orc.trace_full(r), f"no obliquity prec {prec}")

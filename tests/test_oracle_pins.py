@@ -329,6 +329,32 @@ def test_point_emitter_spherical_wave(oracle_mod):
     assert np.max(np.abs(U - want)) <= 1e-9 * np.max(np.abs(want))
 
 
+def test_point_emitter_without_obliquity_is_the_spherical_wave(oracle_mod):
+    """With the obliquity factor left out, a point emitter gives exactly a e^{ikr} / r inside the
+    cone (the analytic spherical wave), and every traced sample loses exactly its cos(theta)."""
+    pts = [(1e-4, -2e-4, 5e-3, 1e-3)]
+    sc = S.point_emitter_scene(pts)
+    r = S.config0_render(W=48, H=40, spp=1, omit_obliquity=1)
+    U = oracle_mod.Oracle(sc).trace_full(r)[0, 0]
+    lam = r.lambdas[0]
+    ii, jj = np.meshgrid(np.arange(r.W), np.arange(r.H))
+    x = (ii + 0.5 - r.W / 2) * r.pitch
+    y = (jj + 0.5 - r.H / 2) * r.pitch
+    cmax = math.sqrt(1 - (lam / (2 * r.pitch)) ** 2)
+    px, py, pz, a = pts[0]
+    rr = np.sqrt((px - x) ** 2 + (py - y) ** 2 + pz ** 2)
+    want = np.where(pz / rr >= cmax, a * np.exp(2j * np.pi * rr / lam) / rr, 0)
+    assert np.count_nonzero(want) > 100
+    assert np.max(np.abs(U - want)) <= 1e-9 * np.max(np.abs(want))
+    o = oracle_mod.Oracle(S.config1_scene())
+    r1 = S.config1_render(W=32, H=24, spp=4, K=1)
+    r0 = S.config1_render(W=32, H=24, spp=4, K=1, omit_obliquity=1)
+    for pix, smp in [(3, 0), (300, 2), (700, 3)]:
+        a1, a0 = o.sample(r1, 0, pix, smp), o.sample(r0, 0, pix, smp)
+        if a1["ok"] and a1["re"] != 0:
+            assert abs((a1["re"] + 1j * a1["im"]) / (a0["re"] + 1j * a0["im"]) - a1["cos"]) < 1e-12
+
+
 def test_conditioning_flags_and_bound(oracle_mod):
     """Per-pixel flags: bits 16-31 count ill-conditioned samples, bits 32-47 samples whose
     incoherent path met a mirror or dielectric; sens bounds the field change that float32-sized
