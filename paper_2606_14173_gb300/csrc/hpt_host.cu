@@ -879,12 +879,8 @@ static void carve_paths(void *arena, size_t B, PathBufs &b)
     b.betac = (float *)take(4 * B);
     b.cost = (float *)take(4 * B);
     b.cv = (int *)take(4 * B);
-    b.L = (float *)take(4 * B);
-    b.beta = (float *)take(4 * B);
-    b.ppdf = (float *)take(4 * B);
-    b.tprev = (float *)take(4 * B);
-    b.nee = (float *)take(4 * B);
-    b.vfl = (int *)take(4 * B);
+    b.inc = (float4 *)take(16 * B);
+    b.inc2 = (float2 *)take(8 * B);
     b.ray_o = (float4 *)take(16 * B);
     b.ray_d = (float4 *)take(16 * B);
     b.sh_d = (float4 *)take(16 * B);

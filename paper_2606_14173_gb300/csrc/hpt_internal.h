@@ -133,8 +133,8 @@ struct PathBufs {
     void *co[3], *cd[3], *opl;           // coherent origin, direction, optical path length
     float *ncur, *betac, *cost;          // medium index, delta-chain throughput, cos(theta) of the sample
     int *cv;                             // coherent vertex count
-    float *L, *beta, *ppdf, *tprev, *nee;
-    int *vfl;                            // incoherent vertex | flags
+    float4 *inc;                         // incoherent state: radiance L, throughput, last BSDF pdf, last distance
+    float2 *inc2;                        // pending NEE contribution, vertex count | flags (int bits)
     float4 *ray_o, *ray_d, *sh_d;        // float ray (origin | tmax, direction | skip), shadow direction | tmax
     float4 *hit;                         // t, u, v, triangle
     int *occl;                           // shadow ray blocked

@@ -116,9 +116,8 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
         // cell centre in a direction uniform on the sphere, drawn at vertex 0
         if (p == 0) scr->qcount[0][1] = wd.n_paths;
         pb.q[1][0][p] = id.valid ? p : (p | Q_FINALIZE);
-        pb.vfl[p] = 0;
-        pb.L[p] = 0.0f;
-        pb.nee[p] = 0.0f;
+        pb.inc[p] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+        pb.inc2[p] = make_float2(0.0f, __int_as_float(0));
         if (!id.valid) return;
         const DevJob &J = *id.J;
         const float4 u = path_draw(J, id.pix, (unsigned)id.s, 0u, 0u, (unsigned)id.lam);
@@ -130,10 +129,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
                             J.bake_lo[2] + ((float)iz + 0.5f) * J.bake_h[2]);
         pb.ray_o[p] = make_float4(x.x, x.y, x.z, 1e30f);
         pb.ray_d[p] = make_float4(st * cp, st * sp, ct, __int_as_float(-1));
-        pb.beta[p] = 1.0f;
-        pb.ppdf[p] = 0.0f;
-        pb.tprev[p] = 0.0f;
-        pb.vfl[p] = VF_PREV_DELTA | VF_BAKE;
+        pb.inc2[p] = make_float2(0.0f, __int_as_float(VF_PREV_DELTA | VF_BAKE));
         return;
     }
     // the first coherent queue is the identity; paths of pixels outside a ragged SLM are marked
@@ -174,7 +170,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
     pb.betac[p] = 1.0f;
     pb.cost[p] = RO::to_f(ct);
     pb.cv[p] = 0;
-    pb.vfl[p] = 0;
+    pb.inc2[p] = make_float2(0.0f, __int_as_float(0));
     const float3 of = tof3(co), df_ = tof3(cd);
     pb.ray_o[p] = make_float4(of.x, of.y, of.z, 1e30f);
     pb.ray_d[p] = make_float4(df_.x, df_.y, df_.z, __int_as_float(-1));
@@ -549,12 +545,8 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                     // the incoherent part starts at P: handed to this iteration's incoherent
                     // shading as a hit at distance 0 from P (vertex count cv after its increment),
                     // so that the coherent kernel carries no BSDF / NEE code
-                    pb.L[p] = 0.0f;
-                    pb.beta[p] = 1.0f;
-                    pb.ppdf[p] = 0.0f;
-                    pb.tprev[p] = 0.0f;
-                    pb.nee[p] = 0.0f;
-                    pb.vfl[p] = (cv - 1) | VF_PREV_DELTA | VF_INC_FIRST | VF_HASP;
+                    pb.inc[p] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+                    pb.inc2[p] = make_float2(0.0f, __int_as_float((cv - 1) | VF_PREV_DELTA | VF_INC_FIRST | VF_HASP));
                     pb.ray_o[p] = make_float4(Pf.x, Pf.y, Pf.z, 1e30f);
                     pb.ray_d[p] = make_float4(dl.x, dl.y, dl.z, __int_as_float(tri));
                     pb.hit[p] = make_float4(0.0f, bb1, bb2, __int_as_float(tri));
@@ -628,12 +620,14 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                 }
             }
         } else {
-            st.L = pb.L[p];
-            st.beta = pb.beta[p];
-            st.ppdf = pb.ppdf[p];
-            st.tprev = pb.tprev[p];
-            st.nee = pb.nee[p];
-            st.vfl = pb.vfl[p];
+            const float4 s4 = pb.inc[p];
+            const float2 s2 = pb.inc2[p];
+            st.L = s4.x;
+            st.beta = s4.y;
+            st.ppdf = s4.z;
+            st.tprev = s4.w;
+            st.nee = s2.x;
+            st.vfl = __float_as_int(s2.y);
             // the NEE of the previous vertex lands first, as in the sequential estimator
             if (st.nee > 0.0f && !pb.occl[p]) st.L += st.nee;
             st.nee = 0.0f;
@@ -662,12 +656,8 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                 pb.amp[p] = (st.vfl & VF_BAKE) ? st.L
                             : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
             } else {
-                pb.L[p] = st.L;
-                pb.beta[p] = st.beta;
-                pb.ppdf[p] = st.ppdf;
-                pb.tprev[p] = st.tprev;
-                pb.nee[p] = st.nee;
-                pb.vfl[p] = st.vfl;
+                pb.inc[p] = make_float4(st.L, st.beta, st.ppdf, st.tprev);
+                pb.inc2[p] = make_float2(st.nee, __int_as_float(st.vfl));
             }
         }
     }
