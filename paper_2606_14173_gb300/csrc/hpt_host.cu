@@ -875,10 +875,7 @@ static void carve_paths(void *arena, size_t B, PathBufs &b)
     for (int k = 0; k < 3; ++k) b.co[k] = take(8 * B);
     for (int k = 0; k < 3; ++k) b.cd[k] = take(8 * B);
     b.opl = take(8 * B);
-    b.ncur = (float *)take(4 * B);
-    b.betac = (float *)take(4 * B);
-    b.cost = (float *)take(4 * B);
-    b.cv = (int *)take(4 * B);
+    b.coh4 = (float4 *)take(16 * B);
     b.inc = (float4 *)take(16 * B);
     b.inc2 = (float2 *)take(8 * B);
     b.ray_o = (float4 *)take(16 * B);

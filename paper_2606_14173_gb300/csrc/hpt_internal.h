@@ -131,8 +131,8 @@ struct WaveDesc {
 // quantities are 8-byte slots holding a double or a double-float (hi, lo) pair.
 struct PathBufs {
     void *co[3], *cd[3], *opl;           // coherent origin, direction, optical path length
-    float *ncur, *betac, *cost;          // medium index, delta-chain throughput, cos(theta) of the sample
-    int *cv;                             // coherent vertex count
+    float4 *coh4;                        // medium index, delta-chain throughput, cos(theta) of the sample,
+                                         // coherent vertex count (int bits)
     float4 *inc;                         // incoherent state: radiance L, throughput, last BSDF pdf, last distance
     float2 *inc2;                        // pending NEE contribution, vertex count | flags (int bits)
     float4 *ray_o, *ray_d, *sh_d;        // float ray (origin | tmax, direction | skip), shadow direction | tmax

@@ -166,10 +166,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
     RS<R>::st(pb.cd[1], p, cd.y);
     RS<R>::st(pb.cd[2], p, cd.z);
     RS<R>::st(pb.opl, p, RO::f(0.0f));
-    pb.ncur[p] = 1.0f;
-    pb.betac[p] = 1.0f;
-    pb.cost[p] = RO::to_f(ct);
-    pb.cv[p] = 0;
+    pb.coh4[p] = make_float4(1.0f, 1.0f, RO::to_f(ct), __int_as_float(0));
     pb.inc2[p] = make_float2(0.0f, __int_as_float(0));
     const float3 of = tof3(co), df_ = tof3(cd);
     pb.ray_o[p] = make_float4(of.x, of.y, of.z, 1e30f);
@@ -261,7 +258,8 @@ __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const Job
                 if (STATS) cnt.refines++;
                 const R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
                 const R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
-                const R tmin = pb.cv[p] > 0 ? RO::fromd(COH_TMIN) : RO::f(0.0f);
+                const bool cont = __float_as_int(pb.coh4[p].w) > 0;   // a continuation after a delta vertex
+                const R tmin = cont ? RO::fromd(COH_TMIN) : RO::f(0.0f);
                 int best = -1;
                 R bt = RO::f(0.0f);
                 if (cand.n <= NCAND) {
@@ -282,7 +280,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const Job
                     if (STATS) cnt.fallbacks++;
                     double tt;
                     tri = traverse_fp64<TRACE_BLOCK>(sc, RO::to_d(co.x), RO::to_d(co.y), RO::to_d(co.z), RO::to_d(cd.x),
-                                                     RO::to_d(cd.y), RO::to_d(cd.z), pb.cv[p] > 0 ? COH_TMIN : 0.0, skip,
+                                                     RO::to_d(cd.y), RO::to_d(cd.z), cont ? COH_TMIN : 0.0, skip,
                                                      &tt, stk, status);
                 }
             }
@@ -486,7 +484,8 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                 R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
                 R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
                 R opl = RS<R>::ld(pb.opl, p);
-                const float ncur = pb.ncur[p];
+                const float4 c4 = pb.coh4[p];
+                const float ncur = c4.x;
                 // distance to the triangle's plane n . x = d0 in the coherent arithmetic
                 const int rb = tri * REF_N;
                 const R3<R> n = r3<R>(RO::load(sc.ref64, sc.refdf, rb), RO::load(sc.ref64, sc.refdf, rb + 1),
@@ -495,7 +494,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                 const R t = (d0 - rdot(n, co)) / rdot(n, cd);
                 const R3<R> P = co + scale(cd, t);
                 opl = opl + RO::mulf(t, ncur);        // OPL = sum n_i L_i (Sec. 4.2)
-                const int cv = pb.cv[p] + 1;
+                const int cv = __float_as_int(c4.w) + 1;
                 const uint4 ix = __ldg(sc.tri_attr + tri);
                 const int kind = sc.mats[ix.w].kind;
                 float3 ng = xyz(__ldg(sc.tri_ng + tri));
@@ -540,7 +539,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                         pb.cz[p] = RO::floor_i(P.z * ih);
                     }
                     // Eq. 2 with the obliquity factor cos(theta) (unless omitted)
-                    pb.basep[p] = (J.obliquity ? pb.cost[p] : 1.0f) * RO::to_f(opl) /
+                    pb.basep[p] = (J.obliquity ? c4.z : 1.0f) * RO::to_f(opl) /
                                   (J.pdf_w[id.lam] * cosP * J.lambda_f[id.lam]);
                     // the incoherent part starts at P: handed to this iteration's incoherent
                     // shading as a hit at distance 0 from P (vertex count cv after its increment),
@@ -568,7 +567,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                     const bool front = dot3(tof3(wo_r), ng) > 0.0f;
                     R3<R> wi = cd;
                     bool ok = true;
-                    float betac = pb.betac[p], nnew = ncur;
+                    float betac = c4.y, nnew = ncur;
                     if (kind == 2) {
                         if (!front) { ns = neg(ns); ng = -ng; }
                         const R c = rdot(wo_r, ns);
@@ -609,9 +608,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                         RS<R>::st(pb.cd[1], p, wi.y);
                         RS<R>::st(pb.cd[2], p, wi.z);
                         RS<R>::st(pb.opl, p, opl);
-                        pb.ncur[p] = nnew;
-                        pb.betac[p] = betac;
-                        pb.cv[p] = cv;
+                        pb.coh4[p] = make_float4(nnew, betac, c4.z, __int_as_float(cv));
                         const float3 pf = tof3(P), wf = tof3(wi);
                         pb.ray_o[p] = make_float4(pf.x, pf.y, pf.z, 1e30f);
                         pb.ray_d[p] = make_float4(wf.x, wf.y, wf.z, __int_as_float(tri));
@@ -646,7 +643,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
             if (!do_vertex) {
                 if (STATS) cnt.samples++;
                 pb.amp[p] = (st.vfl & VF_BAKE) ? st.L
-                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
+                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.coh4[p].y * st.L) : 0.0f;
             }
         }
         if (do_vertex) {
@@ -654,7 +651,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
             if (done) {
                 if (STATS) cnt.samples++;
                 pb.amp[p] = (st.vfl & VF_BAKE) ? st.L
-                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.betac[p] * st.L) : 0.0f;
+                            : (st.vfl & VF_HASP) ? pb.basep[p] * sqrtf(pb.coh4[p].y * st.L) : 0.0f;
             } else {
                 pb.inc[p] = make_float4(st.L, st.beta, st.ppdf, st.tprev);
                 pb.inc2[p] = make_float2(st.nee, __int_as_float(st.vfl));
