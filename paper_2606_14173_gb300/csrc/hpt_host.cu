@@ -872,9 +872,10 @@ static void carve_paths(void *arena, size_t B, PathBufs &b)
         p += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    for (int k = 0; k < 3; ++k) b.co[k] = take(8 * B);
-    for (int k = 0; k < 3; ++k) b.cd[k] = take(8 * B);
-    b.opl = take(8 * B);
+    b.cs0 = (uint4 *)take(16 * B);
+    b.cs1 = (uint4 *)take(16 * B);
+    b.cs2 = (uint4 *)take(16 * B);
+    b.cs3 = (uint2 *)take(8 * B);
     b.coh4 = (float4 *)take(16 * B);
     b.inc = (float4 *)take(16 * B);
     b.inc2 = (float2 *)take(8 * B);

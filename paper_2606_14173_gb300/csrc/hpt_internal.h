@@ -130,7 +130,10 @@ struct WaveDesc {
 // Structure-of-arrays state of the paths of one wave (capacity paths each).  The coherent
 // quantities are 8-byte slots holding a double or a double-float (hi, lo) pair.
 struct PathBufs {
-    void *co[3], *cd[3], *opl;           // coherent origin, direction, optical path length
+    // coherent origin o, direction d, optical path length, as 8-byte slots (double or (hi, lo)
+    // floats) packed in 16-byte units: (o.x, o.y), (o.z, d.x), (d.y, d.z), then OPL alone
+    uint4 *cs0, *cs1, *cs2;
+    uint2 *cs3;
     float4 *coh4;                        // medium index, delta-chain throughput, cos(theta) of the sample,
                                          // coherent vertex count (int bits)
     float4 *inc;                         // incoherent state: radiance L, throughput, last BSDF pdf, last distance

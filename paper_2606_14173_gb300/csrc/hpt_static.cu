@@ -61,9 +61,10 @@ Layout carve(void *base)
     L.scr = (SlotScratch *)take(sizeof(SlotScratch));
     const size_t B = (size_t)FIXED_CAPACITY;
     PathBufs &b = L.pb;
-    for (int k = 0; k < 3; ++k) b.co[k] = take(8 * B);
-    for (int k = 0; k < 3; ++k) b.cd[k] = take(8 * B);
-    b.opl = take(8 * B);
+    b.cs0 = (uint4 *)take(16 * B);
+    b.cs1 = (uint4 *)take(16 * B);
+    b.cs2 = (uint4 *)take(16 * B);
+    b.cs3 = (uint2 *)take(8 * B);
     b.coh4 = (float4 *)take(16 * B);
     b.inc = (float4 *)take(16 * B);
     b.inc2 = (float2 *)take(8 * B);

@@ -20,19 +20,53 @@
 
 namespace hpt {
 
+// an 8-byte coherent slot: a double, or a double-float as its two floats' bits
 template <class R> struct RS;
 template <> struct RS<double> {
-    static __device__ __forceinline__ double ld(const void *b, int p) { return ((const double *)b)[p]; }
-    static __device__ __forceinline__ void st(void *b, int p, double v) { ((double *)b)[p] = v; }
+    static __device__ __forceinline__ double from(unsigned a, unsigned b) { return __hiloint2double((int)b, (int)a); }
+    static __device__ __forceinline__ void to(double v, unsigned &a, unsigned &b)
+    {
+        a = (unsigned)__double2loint(v);
+        b = (unsigned)__double2hiint(v);
+    }
 };
 template <> struct RS<df> {
-    static __device__ __forceinline__ df ld(const void *b, int p)
+    static __device__ __forceinline__ df from(unsigned a, unsigned b) { return mkdf(__uint_as_float(a), __uint_as_float(b)); }
+    static __device__ __forceinline__ void to(df v, unsigned &a, unsigned &b)
     {
-        float2 v = ((const float2 *)b)[p];
-        return mkdf(v.x, v.y);
+        a = __float_as_uint(v.hi);
+        b = __float_as_uint(v.lo);
     }
-    static __device__ __forceinline__ void st(void *b, int p, df v) { ((float2 *)b)[p] = make_float2(v.hi, v.lo); }
 };
+
+// the coherent state of path p: origin, direction and optical path length
+template <class R>
+__device__ __forceinline__ void coh_load(const PathBufs &pb, int p, R3<R> &o, R3<R> &d, R &opl)
+{
+    const uint4 a = pb.cs0[p], b = pb.cs1[p], c = pb.cs2[p];
+    const uint2 e = pb.cs3[p];
+    o = r3<R>(RS<R>::from(a.x, a.y), RS<R>::from(a.z, a.w), RS<R>::from(b.x, b.y));
+    d = r3<R>(RS<R>::from(b.z, b.w), RS<R>::from(c.x, c.y), RS<R>::from(c.z, c.w));
+    opl = RS<R>::from(e.x, e.y);
+}
+
+template <class R>
+__device__ __forceinline__ void coh_store(const PathBufs &pb, int p, const R3<R> &o, const R3<R> &d, R opl)
+{
+    uint4 a, b, c;
+    uint2 e;
+    RS<R>::to(o.x, a.x, a.y);
+    RS<R>::to(o.y, a.z, a.w);
+    RS<R>::to(o.z, b.x, b.y);
+    RS<R>::to(d.x, b.z, b.w);
+    RS<R>::to(d.y, c.x, c.y);
+    RS<R>::to(d.z, c.z, c.w);
+    RS<R>::to(opl, e.x, e.y);
+    pb.cs0[p] = a;
+    pb.cs1[p] = b;
+    pb.cs2[p] = c;
+    pb.cs3[p] = e;
+}
 
 enum : int { VF_V = 0xFF, VF_PREV_DELTA = 1 << 8, VF_INC_FIRST = 1 << 9, VF_HASP = 1 << 10, VF_BAKE = 1 << 11 };
 constexpr int Q_FINALIZE = (int)0x80000000;
@@ -159,13 +193,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen(const JobTable *__restrict__ 
         co = r3<R>(rdot(c0, q), rdot(c1, q), rdot(c2, q));
         cd = r3<R>(rdot(c0, dh), rdot(c1, dh), rdot(c2, dh));
     }
-    RS<R>::st(pb.co[0], p, co.x);
-    RS<R>::st(pb.co[1], p, co.y);
-    RS<R>::st(pb.co[2], p, co.z);
-    RS<R>::st(pb.cd[0], p, cd.x);
-    RS<R>::st(pb.cd[1], p, cd.y);
-    RS<R>::st(pb.cd[2], p, cd.z);
-    RS<R>::st(pb.opl, p, RO::f(0.0f));
+    coh_store<R>(pb, p, co, cd, RO::f(0.0f));
     pb.coh4[p] = make_float4(1.0f, 1.0f, RO::to_f(ct), __int_as_float(0));
     pb.inc2[p] = make_float2(0.0f, __int_as_float(0));
     const float3 of = tof3(co), df_ = tof3(cd);
@@ -256,8 +284,9 @@ __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const Job
                 // float winner) in the coherent arithmetic; a full double traversal only when the
                 // list overflowed or no candidate holds
                 if (STATS) cnt.refines++;
-                const R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
-                const R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
+                R3<R> co, cd;
+                R opl_unused;
+                coh_load<R>(pb, p, co, cd, opl_unused);
                 const bool cont = __float_as_int(pb.coh4[p].w) > 0;   // a continuation after a delta vertex
                 const R tmin = cont ? RO::fromd(COH_TMIN) : RO::f(0.0f);
                 int best = -1;
@@ -481,9 +510,9 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
         if constexpr (COH) {
             const int tri = __float_as_int(pb.hit[p].w);
             if (tri >= 0) {
-                R3<R> co = r3<R>(RS<R>::ld(pb.co[0], p), RS<R>::ld(pb.co[1], p), RS<R>::ld(pb.co[2], p));
-                R3<R> cd = r3<R>(RS<R>::ld(pb.cd[0], p), RS<R>::ld(pb.cd[1], p), RS<R>::ld(pb.cd[2], p));
-                R opl = RS<R>::ld(pb.opl, p);
+                R3<R> co, cd;
+                R opl;
+                coh_load<R>(pb, p, co, cd, opl);
                 const float4 c4 = pb.coh4[p];
                 const float ncur = c4.x;
                 // distance to the triangle's plane n . x = d0 in the coherent arithmetic
@@ -601,13 +630,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const Job
                         }
                     }
                     if (ok) {
-                        RS<R>::st(pb.co[0], p, P.x);
-                        RS<R>::st(pb.co[1], p, P.y);
-                        RS<R>::st(pb.co[2], p, P.z);
-                        RS<R>::st(pb.cd[0], p, wi.x);
-                        RS<R>::st(pb.cd[1], p, wi.y);
-                        RS<R>::st(pb.cd[2], p, wi.z);
-                        RS<R>::st(pb.opl, p, opl);
+                        coh_store<R>(pb, p, P, wi, opl);
                         pb.coh4[p] = make_float4(nnew, betac, c4.z, __int_as_float(cv));
                         const float3 pf = tof3(P), wf = tof3(wi);
                         pb.ray_o[p] = make_float4(pf.x, pf.y, pf.z, 1e30f);
