@@ -2,8 +2,9 @@
 // (hpt_grf_build) and the angular spectrum method of the two-stage scheme (hpt_asm_propagate).
 //
 // Both rest on one 2-D FFT of power-of-two sizes: every row transformed in shared memory by
-// one block (Stockham autosort, radix 4 with one radix-2 step for odd powers of two, two
-// shared buffers so that the global loads and stores stay in natural order), a tiled
+// one block (Stockham autosort: radix-16 passes in registers, the remainder radix first, the
+// first pass reading global memory and the last writing it in natural order, shared buffers
+// in between), a tiled
 // transpose, the rows again, and the transpose back.  The data are complex64; the twiddle factors are rounded
 // from double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
 // ~1e5 turns, is formed in double before its fraction is taken.
@@ -27,8 +28,8 @@ using namespace hpt;
 
 namespace {
 
-constexpr int FFT_MAX_LOG = 13;          // 8192 points: 2 x 64 KB of shared memory per row
-constexpr int FFT_THREADS = 256;
+constexpr int FFT_MAX_LOG = 13;          // 8192 points: 2 (3 for the ASM pass) x 64 KB of shared memory
+constexpr int FFT_THREADS = 512;
 constexpr unsigned GRF_TAG = 0x47524600u;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -46,56 +47,115 @@ __global__ void k_twiddles(float2 *tw, int n)
     tw[k] = make_float2((float)c, (float)s);
 }
 
-// FFT of one row of n = 2^logn points held in shared memory x, with y as the second Stockham
-// buffer; sign = -1: forward (exp(-2 pi i k j / n)), +1: inverse without the 1/n.  Returns the
-// buffer that holds the result.  Stockham stages: with Ns the length of the sub-transforms
-// already done and R the radix, element j of the stage reads x[j + r n/R] (r < R), multiplies
-// it by exp(sign 2 pi i r (j mod Ns) / (Ns R)), takes the R-point DFT and writes it to
-// y[(j / Ns) Ns R + j mod Ns + r Ns].  Radix 4, with one radix-2 step first for odd logn.
-// The caller synchronises before (x filled) and the function ends with a barrier.
-__device__ float2 *fft_smem(float2 *x, float2 *y, int logn, float sign, const float2 *__restrict__ tw)
+// exp(-2 pi i m / 16), m < 8: the constants of the in-register radix-16 DFT
+__device__ __forceinline__ float2 w16(int m)
 {
-    const int n = 1 << logn;
-    int Ns = 1;
-    if (logn & 1) {
-        for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
-            const float2 a = x[j], b = x[j + n / 2];
-            y[2 * j] = make_float2(a.x + b.x, a.y + b.y);
-            y[2 * j + 1] = make_float2(a.x - b.x, a.y - b.y);
-        }
-        __syncthreads();
-        float2 *t = x; x = y; y = t;
-        Ns = 2;
-    }
-    for (; Ns < n; Ns *= 4) {
-        const int q = n / 4, tws = n / (Ns * 4);
-        for (int j = threadIdx.x; j < q; j += blockDim.x) {
-            const int k = j & (Ns - 1);
-            float2 v0 = x[j], v1 = x[j + q], v2 = x[j + 2 * q], v3 = x[j + 3 * q];
-            if (Ns > 1) {
-                float2 w1 = __ldg(tw + k * tws), w2 = __ldg(tw + 2 * k * tws), w3 = __ldg(tw + 3 * k * tws);
-                w1.y *= -sign;
-                w2.y *= -sign;
-                w3.y *= -sign;
-                v1 = cmul(v1, w1);
-                v2 = cmul(v2, w2);
-                v3 = cmul(v3, w3);
-            }
-            // 4-point DFT; forward uses -i, inverse +i
-            const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
-            const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
-            const float2 id13 = make_float2(-sign * d13.y, sign * d13.x);   // sign * i * d13
-            const int o = (j - k) * 4 + k;
-            y[o] = make_float2(s02.x + s13.x, s02.y + s13.y);
-            y[o + Ns] = make_float2(d02.x + id13.x, d02.y + id13.y);
-            y[o + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
-            y[o + 3 * Ns] = make_float2(d02.x - id13.x, d02.y - id13.y);
-        }
-        __syncthreads();
-        float2 *t = x; x = y; y = t;
-    }
-    return x;
+    const float c[8] = {1.0f, 0.923879533f, 0.707106781f, 0.382683432f, 0.0f, -0.382683432f, -0.707106781f, -0.923879533f};
+    const float s[8] = {0.0f, 0.382683432f, 0.707106781f, 0.923879533f, 1.0f, 0.923879533f, 0.707106781f, 0.382683432f};
+    return make_float2(c[m], -s[m]);
 }
+
+// R-point DFT of v in registers (R = 2, 4, 8, 16): bit-reversed order, then log2 R radix-2
+// stages; sign = -1 forward, +1 inverse
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 *v, float sign)
+{
+    constexpr int B = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    float2 t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 0; b < B; ++b) r |= ((i >> b) & 1) << (B - 1 - b);
+        t[r] = v[i];
+    }
+#pragma unroll
+    for (int half = 1; half < R; half *= 2) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * half) {
+#pragma unroll
+            for (int pos = 0; pos < half; ++pos) {
+                float2 w = w16(pos * (8 / half));
+                w.y *= -sign;
+                const float2 a = t[g + pos], b = cmul(w, t[g + pos + half]);
+                t[g + pos] = make_float2(a.x + b.x, a.y + b.y);
+                t[g + pos + half] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// One Stockham pass of radix R over n points: element j of the pass reads x[j + r n/R]
+// (r < R) through 'ld', multiplies it by exp(sign 2 pi i r (j mod Ns) / (Ns R)) (the n-point
+// twiddle table), takes the R-point DFT and writes y[(j - j mod Ns) R + j mod Ns + r Ns]
+// through 'st'.
+template <int R, class LD, class ST>
+__device__ __forceinline__ void stockham_pass(int n, int Ns, float sign, const float2 *__restrict__ tw, LD ld, ST st)
+{
+    const int q = n / R, tws = n / (Ns * R);
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        const int k = j & (Ns - 1);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 a = ld(j + r * q);
+            if (r > 0 && Ns > 1) {
+                float2 w = __ldg(tw + r * k * tws);
+                w.y *= -sign;
+                a = cmul(a, w);
+            }
+            v[r] = a;
+        }
+        dft_reg<R>(v, sign);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) st(o + r * Ns, v[r]);
+    }
+}
+
+template <class LD, class ST>
+__device__ __forceinline__ void pass_any(int R, int n, int Ns, float sign, const float2 *tw, LD ld, ST st)
+{
+    switch (R) {
+    case 2: stockham_pass<2>(n, Ns, sign, tw, ld, st); break;
+    case 4: stockham_pass<4>(n, Ns, sign, tw, ld, st); break;
+    case 8: stockham_pass<8>(n, Ns, sign, tw, ld, st); break;
+    default: stockham_pass<16>(n, Ns, sign, tw, ld, st); break;
+    }
+}
+
+// FFT of one row of n = 2^logn points: radix 16 passes (the remainder radix first), input
+// through 'gld' (global memory or shared), output through 'gst', the passes in between in the
+// shared buffers a and b.  The first pass reads gld, the last writes gst; a one-pass transform
+// goes through a.  Ends with a barrier.
+template <class LD, class ST>
+__device__ __forceinline__ void row_fft(int logn, float sign, const float2 *tw, float2 *a, float2 *b, LD gld, ST gst)
+{
+    const int n = 1 << logn, rem = logn & 3;
+    const int npass = (logn >> 2) + (rem ? 1 : 0);
+    int Ns = 1;
+    for (int p = 0; p < npass; ++p) {
+        const int R = (p == 0 && rem) ? (1 << rem) : 16;
+        float2 *dst = (p & 1) ? b : a;
+        const float2 *src = (p & 1) ? a : b;
+        const bool first = p == 0, last = p == npass - 1 && npass > 1;
+        auto sld = [&](int i) { return src[i]; };
+        auto sst = [&](int i, float2 v) { dst[i] = v; };
+        if (first) pass_any(R, n, Ns, sign, tw, gld, sst);
+        else if (last) pass_any(R, n, Ns, sign, tw, sld, gst);
+        else pass_any(R, n, Ns, sign, tw, sld, sst);
+        __syncthreads();
+        Ns *= R;
+    }
+    if (npass == 1) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) gst(i, a[i]);
+        __syncthreads();
+    }
+}
+
+__host__ __device__ constexpr int fft_threads(int n) { return n / 16 > 32 ? (n / 16 < FFT_THREADS ? n / 16 : FFT_THREADS) : 32; }
 
 // In-place FFT of 'rows' consecutive rows of n = 2^logn points, times 'scale'.
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_rows(float2 *data, int logn, int rows, float sign,
@@ -105,14 +165,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_rows(float2 *data, int logn
     const int n = 1 << logn;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         float2 *d = data + (size_t)row * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
-        __syncthreads();
-        const float2 *r = fft_smem(sm, sm + n, logn, sign, tw);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const float2 v = r[i];
-            d[i] = make_float2(v.x * scale, v.y * scale);
-        }
-        __syncthreads();
+        row_fft(logn, sign, tw, sm, sm + n, [&](int i) { return d[i]; },
+                [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
     }
 }
 
@@ -132,37 +186,31 @@ __global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_in(const float2 *__res
             continue;
         }
         const float2 *src = in + (size_t)y * W;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int x = i - ox;
-            sm[i] = (x >= 0 && x < W) ? src[x] : make_float2(0.0f, 0.0f);
-        }
-        __syncthreads();
-        const float2 *r = fft_smem(sm, sm + n, logn, -1.0f, tw);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = r[i];
-        __syncthreads();
+        row_fft(logn, -1.0f, tw, sm, sm + n,
+                [&](int i) {
+                    const int x = i - ox;
+                    return (x >= 0 && x < W) ? src[x] : make_float2(0.0f, 0.0f);
+                },
+                [&](int i, float2 v) { d[i] = v; });
     }
 }
 
 // ASM pass 2, on the transposed spectrum (one row per spatial frequency fx): forward FFT of the
-// row, multiplication by the transfer function's row (scale folded in), inverse FFT.
+// row, multiplication by the transfer function's row (scale folded in) on the way into shared
+// memory, inverse FFT.
 __global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_conv(float2 *data, int logn, int rows,
                                                                const float2 *__restrict__ Ht,
                                                                const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
     const int n = 1 << logn;
+    float2 *a = sm, *b = sm + n, *c = sm + 2 * n;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         float2 *d = data + (size_t)row * n;
         const float2 *h = Ht + (size_t)row * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
-        __syncthreads();
-        float2 *r = fft_smem(sm, sm + n, logn, -1.0f, tw);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = cmul(r[i], __ldg(h + i));
-        __syncthreads();
-        float2 *other = r == sm ? sm + n : sm;
-        const float2 *q = fft_smem(r, other, logn, +1.0f, tw);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q[i];
-        __syncthreads();
+        row_fft(logn, -1.0f, tw, a, b, [&](int i) { return d[i]; },
+                [&](int i, float2 v) { c[i] = cmul(v, __ldg(h + i)); });
+        row_fft(logn, +1.0f, tw, a, b, [&](int i) { return c[i]; }, [&](int i, float2 v) { d[i] = v; });
     }
 }
 
@@ -175,12 +223,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_out(const float2 *__re
     const int n = 1 << logn;
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         const float2 *d = data + (size_t)(y + oy) * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = d[i];
-        __syncthreads();
-        const float2 *r = fft_smem(sm, sm + n, logn, +1.0f, tw);
         float2 *dst = out + (size_t)y * W;
-        for (int x = threadIdx.x; x < W; x += blockDim.x) dst[x] = r[x + ox];
-        __syncthreads();
+        row_fft(logn, +1.0f, tw, sm, sm + n, [&](int i) { return d[i]; },
+                [&](int i, float2 v) {
+                    const int x = i - ox;
+                    if (x >= 0 && x < W) dst[x] = v;
+                });
     }
 }
 
@@ -270,10 +318,10 @@ cudaError_t fft2d(float2 *A, float2 *B, int nx, int ny, const float2 *twx, const
 {
     const int lx = ilog2(nx), ly = ilog2(ny);
     const dim3 tb(32, 8);
-    k_fft_rows<<<std::min(ny, 152 * 8), std::min(FFT_THREADS, std::max(32, nx / 4)), 2 * sizeof(float2) * nx, s>>>(
+    k_fft_rows<<<std::min(ny, 152 * 8), fft_threads(nx), 2 * sizeof(float2) * nx, s>>>(
         A, lx, ny, sign, twx, 1.0f);
     k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
-    k_fft_rows<<<std::min(nx, 152 * 8), std::min(FFT_THREADS, std::max(32, ny / 4)), 2 * sizeof(float2) * ny, s>>>(
+    k_fft_rows<<<std::min(nx, 152 * 8), fft_threads(ny), 2 * sizeof(float2) * ny, s>>>(
         B, ly, nx, sign, twy, scale);
     k_transpose<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, A, ny, nx);
     return cudaGetLastError();
@@ -283,7 +331,7 @@ cudaError_t fft_setup()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    const int smem = (int)(2 * sizeof(float2)) << FFT_MAX_LOG;
+    const int smem = (int)(3 * sizeof(float2)) << FFT_MAX_LOG;
     cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_in, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -353,13 +401,13 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, const flo
     // rows of the padded field -> transpose -> per-frequency rows: FFT, transfer, inverse FFT
     // -> transpose -> inverse FFT of the window's rows, cropped
     const dim3 tb(32, 8);
-    k_asm_rows_in<<<std::min(P.Hp, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Wp / 4)), 2 * sizeof(float2) * P.Wp,
+    k_asm_rows_in<<<std::min(P.Hp, 152 * 8), fft_threads(P.Wp), 2 * sizeof(float2) * P.Wp,
                     s>>>(in, P.A, P.lx, P.Hp, P.W, P.H, P.ox, P.oy, P.twx);
     k_transpose<<<dim3((P.Wp + 31) / 32, (P.Hp + 31) / 32), tb, 0, s>>>(P.A, P.B, P.Wp, P.Hp);
-    k_asm_rows_conv<<<std::min(P.Wp, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Hp / 4)),
-                      2 * sizeof(float2) * P.Hp, s>>>(P.B, P.ly, P.Wp, Ht, P.twy);
+    k_asm_rows_conv<<<std::min(P.Wp, 152 * 8), fft_threads(P.Hp), 3 * sizeof(float2) * P.Hp, s>>>(P.B, P.ly, P.Wp,
+                                                                                                   Ht, P.twy);
     k_transpose<<<dim3((P.Hp + 31) / 32, (P.Wp + 31) / 32), tb, 0, s>>>(P.B, P.A, P.Hp, P.Wp);
-    k_asm_rows_out<<<std::min(P.H, 152 * 8), std::min(FFT_THREADS, std::max(32, P.Wp / 4)), 2 * sizeof(float2) * P.Wp,
+    k_asm_rows_out<<<std::min(P.H, 152 * 8), fft_threads(P.Wp), 2 * sizeof(float2) * P.Wp,
                      s>>>(P.A, out, P.lx, P.W, P.H, P.ox, P.oy, P.twx);
     return cudaGetLastError();
 }
