@@ -276,10 +276,11 @@ def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
     asm_ms = timed_ms(lambda: ctx.asm_propagate(out, r.lambdas, r.pitch, 80e-3, out=res, stream=stream))
     Wp = Hp = 4096
     n_fields = len(r.lambdas) * r.K
-    # algorithmic bytes per field: two 2-D FFTs of four row passes' worth of read + write each
-    # (a 2-D FFT needs every element read and written once per dimension and direction), the
-    # transfer function read once, the field read and written once
-    alg = n_fields * (2 * 2 * 2 * 8 * Wp * Hp + 8 * Wp * Hp + 2 * 8 * r.W * r.H)
+    # algorithmic bytes of the row-column ASM that skips the zero padding: every field read and
+    # written once; its spectrum (H rows of Wp) written by the forward x pass, read and written
+    # by the y pass (FFT, transfer, inverse FFT, the window's rows kept) and read by the inverse
+    # x pass; the transfer function of each wavelength read once
+    alg = n_fields * 8 * (2 * r.W * r.H + 4 * Wp * r.H) + len(r.lambdas) * 8 * Wp * Hp
     achieved = alg / (asm_ms / 1e3) / 1e9
     rg = dataclasses.replace(r, phase_mode=2, grf=grf["phi"])
     grf_trace_ms = timed_ms(lambda: ctx.trace(sid, rg, out, precision=hpt.PREC_DF32, stream=stream))

@@ -3,12 +3,13 @@
 //
 // Both rest on one 2-D FFT of power-of-two sizes: every row transformed in shared memory by
 // one block (Stockham autosort: radix-16 passes in registers, the remainder radix first, the
-// first pass reading global memory and the last writing it in natural order, shared buffers
-// in between), a tiled
-// transpose, the rows again, and the transpose back.  The data are complex64; the twiddle factors are rounded
-// from double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
-// ~1e5 turns, is formed in double before its fraction is taken.
+// first pass reading global memory and the last writing it in natural order, the passes in
+// between in place in one bank-padded shared buffer), a tiled transpose, the rows again, and
+// the transpose back.  The data are complex64; the twiddle factors are rounded from
+// double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
+// ~1e5 turns, is formed in double-float arithmetic before its fraction is taken.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,9 +29,13 @@ using namespace hpt;
 
 namespace {
 
-constexpr int FFT_MAX_LOG = 13;          // 8192 points: 2 (3 for the ASM pass) x 64 KB of shared memory
+constexpr int FFT_MAX_LOG = 13;          // 8192 points: 68 KB of shared memory
 constexpr int FFT_THREADS = 512;
+#ifndef HPT_FFT_REGS
+#define HPT_FFT_REGS 64                  // registers per thread the row kernels are compiled for
+#endif
 constexpr unsigned GRF_TAG = 0x47524600u;
+constexpr int ASM_BATCH = 8;             // fields of one wavelength propagated by one group of launches
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -87,155 +92,218 @@ __device__ __forceinline__ void dft_reg(float2 *v, float sign)
     for (int i = 0; i < R; ++i) v[i] = t[i];
 }
 
-// One Stockham pass of radix R over n points: element j of the pass reads x[j + r n/R]
-// (r < R) through 'ld', multiplies it by exp(sign 2 pi i r (j mod Ns) / (Ns R)) (the n-point
-// twiddle table), takes the R-point DFT and writes y[(j - j mod Ns) R + j mod Ns + r Ns]
-// through 'st'.
-template <int R, class LD, class ST>
-__device__ __forceinline__ void stockham_pass(int n, int Ns, float sign, const float2 *__restrict__ tw, LD ld, ST st)
-{
-    const int q = n / R, tws = n / (Ns * R);
-    for (int j = threadIdx.x; j < q; j += blockDim.x) {
-        const int k = j & (Ns - 1);
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 a = ld(j + r * q);
-            if (r > 0 && Ns > 1) {
-                float2 w = __ldg(tw + r * k * tws);
-                w.y *= -sign;
-                a = cmul(a, w);
-            }
-            v[r] = a;
-        }
-        dft_reg<R>(v, sign);
-        const int o = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) st(o + r * Ns, v[r]);
-    }
-}
-
-template <class LD, class ST>
-__device__ __forceinline__ void pass_any(int R, int n, int Ns, float sign, const float2 *tw, LD ld, ST st)
-{
-    switch (R) {
-    case 2: stockham_pass<2>(n, Ns, sign, tw, ld, st); break;
-    case 4: stockham_pass<4>(n, Ns, sign, tw, ld, st); break;
-    case 8: stockham_pass<8>(n, Ns, sign, tw, ld, st); break;
-    default: stockham_pass<16>(n, Ns, sign, tw, ld, st); break;
-    }
-}
-
-// FFT of one row of n = 2^logn points: radix 16 passes (the remainder radix first), input
-// through 'gld' (global memory or shared), output through 'gst', the passes in between in the
-// shared buffers a and b.  The first pass reads gld, the last writes gst; a one-pass transform
-// goes through a.  Ends with a barrier.
-template <class LD, class ST>
-__device__ __forceinline__ void row_fft(int logn, float sign, const float2 *tw, float2 *a, float2 *b, LD gld, ST gst)
-{
-    const int n = 1 << logn, rem = logn & 3;
-    const int npass = (logn >> 2) + (rem ? 1 : 0);
-    int Ns = 1;
-    for (int p = 0; p < npass; ++p) {
-        const int R = (p == 0 && rem) ? (1 << rem) : 16;
-        float2 *dst = (p & 1) ? b : a;
-        const float2 *src = (p & 1) ? a : b;
-        const bool first = p == 0, last = p == npass - 1 && npass > 1;
-        auto sld = [&](int i) { return src[i]; };
-        auto sst = [&](int i, float2 v) { dst[i] = v; };
-        if (first) pass_any(R, n, Ns, sign, tw, gld, sst);
-        else if (last) pass_any(R, n, Ns, sign, tw, sld, gst);
-        else pass_any(R, n, Ns, sign, tw, sld, sst);
-        __syncthreads();
-        Ns *= R;
-    }
-    if (npass == 1) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) gst(i, a[i]);
-        __syncthreads();
-    }
-}
-
+// Shared-memory index of point i of a row: one float2 of padding after every 16, so that the
+// stride-16 stores of the first pass and the strided loads after it fall in distinct banks.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fft_smem_bytes(int n) { return (n + n / 16 + 1) * (int)sizeof(float2); }
+// threads of a row's block: n / 16 (each holds 16 points of a pass), at least one warp
 __host__ __device__ constexpr int fft_threads(int n) { return n / 16 > 32 ? (n / 16 < FFT_THREADS ? n / 16 : FFT_THREADS) : 32; }
-
-// In-place FFT of 'rows' consecutive rows of n = 2^logn points, times 'scale'.
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_rows(float2 *data, int logn, int rows, float sign,
-                                                          const float2 *__restrict__ tw, float scale)
+// resident blocks per SM the row kernels are compiled for: HPT_FFT_REGS registers per thread
+__host__ __device__ constexpr int fft_minb(int n)
 {
-    extern __shared__ float2 sm[];
-    const int n = 1 << logn;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        float2 *d = data + (size_t)row * n;
-        row_fft(logn, sign, tw, sm, sm + n, [&](int i) { return d[i]; },
-                [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
-    }
+    return 65536 / (HPT_FFT_REGS * fft_threads(n)) < 1 ? 1 : (65536 / (HPT_FFT_REGS * fft_threads(n)) > 32 ? 32 : 65536 / (HPT_FFT_REGS * fft_threads(n)));
 }
+// radix of pass p of a 2^logn-point transform (the remainder radix first, then 16s), the number
+// of passes, and the span Ns of the sub-transforms pass p combines
+__host__ __device__ constexpr int fft_radix(int logn, int p) { return (p == 0 && (logn & 3)) ? (1 << (logn & 3)) : 16; }
+__host__ __device__ constexpr int fft_npass(int logn) { return (logn >> 2) + ((logn & 3) ? 1 : 0); }
+__host__ __device__ constexpr int fft_ns(int logn, int p) { return p == 0 ? 1 : fft_ns(logn, p - 1) * fft_radix(logn, p - 1); }
 
-// ASM pass 1: forward FFT of the rows of the zero-padded field.  Row r of the padded grid holds
-// in[r - oy][c - ox] for the window, 0 elsewhere; rows outside the window transform to 0.
-__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_in(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                             int logn, int rows, int W, int H, int ox, int oy,
-                                                             const float2 *__restrict__ tw)
+// Pass P of the Stockham transform of N = 2^LOGN points (radix R, span NS): element j reads
+// x[j + r N/R] (r < R) through 'ld', multiplies it by exp(sign 2 pi i r (j mod NS) / (NS R))
+// (the N-point twiddle table), takes the R-point DFT and writes
+// y[(j - j mod NS) R + j mod NS + r NS] through 'st'.  Thread t takes j = t + m T (T threads,
+// m < J); with 'inplace' every thread holds its values in registers across a barrier before
+// it stores, so that x and y may be the same buffer.
+template <int LOGN, int P, class LD, class ST>
+__device__ __forceinline__ void stockham_pass(float sign, const float2 *__restrict__ tw, LD ld, ST st, bool inplace)
 {
-    extern __shared__ float2 sm[];
-    const int n = 1 << logn;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        float2 *d = out + (size_t)row * n;
-        const int y = row - oy;
-        if (y < 0 || y >= H) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = make_float2(0.0f, 0.0f);
-            continue;
+    constexpr int N = 1 << LOGN, R = fft_radix(LOGN, P), NS = fft_ns(LOGN, P), T = fft_threads(N);
+    constexpr int Q = N / R, TWS = N / (NS * R), J = (Q + T - 1) / T;
+    constexpr bool RAGGED = J * T > Q;
+    float2 v[J][R];
+#pragma unroll
+    for (int m = 0; m < J; ++m) {
+        // past the row (small N only) a thread repeats the last element's loads and stores nothing
+        const int j = RAGGED ? min((int)threadIdx.x + m * T, Q - 1) : (int)threadIdx.x + m * T;
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[m][r] = ld(j + r * Q);
+        if (NS > 1) {
+            // twiddles w^r, w = exp(sign 2 pi i k / (NS R)): w, w^2, w^3 formed from the loaded w,
+            // w^(4c) loaded for c >= 1 and multiplied by them (at most two roundings per twiddle)
+            float2 w1 = __ldg(tw + k * TWS);
+            w1.y *= -sign;
+            const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w;
+                if (r % 4 == 0 || r < 4) {
+                    w = r == 1 ? w1 : r == 2 ? w2 : r == 3 ? w3 : __ldg(tw + r * k * TWS);
+                    if (r >= 4) w.y *= -sign;
+                } else {
+                    float2 b = __ldg(tw + (r & ~3) * k * TWS);
+                    b.y *= -sign;
+                    w = cmul(b, (r & 3) == 1 ? w1 : (r & 3) == 2 ? w2 : w3);
+                }
+                v[m][r] = cmul(v[m][r], w);
+            }
         }
-        const float2 *src = in + (size_t)y * W;
-        row_fft(logn, -1.0f, tw, sm, sm + n,
-                [&](int i) {
-                    const int x = i - ox;
-                    return (x >= 0 && x < W) ? src[x] : make_float2(0.0f, 0.0f);
-                },
-                [&](int i, float2 v) { d[i] = v; });
+        dft_reg<R>(v[m], sign);
+    }
+    if (inplace) __syncthreads();
+#pragma unroll
+    for (int m = 0; m < J; ++m) {
+        const int j = (int)threadIdx.x + m * T;
+        if (!RAGGED || j < Q) {
+            const int k = j & (NS - 1);
+            const int o = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) st(o + r * NS, v[m][r]);
+        }
     }
 }
 
-// ASM pass 2, on the transposed spectrum (one row per spatial frequency fx): forward FFT of the
-// row, multiplication by the transfer function's row (scale folded in) on the way into shared
-// memory, inverse FFT.
-__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_conv(float2 *data, int logn, int rows,
-                                                               const float2 *__restrict__ Ht,
-                                                               const float2 *__restrict__ tw)
+// FFT of one row of 2^LOGN points by fft_threads(2^LOGN) threads: the passes from P on, the
+// first reading through 'gld', the last writing through 'gst', the ones in between in place in
+// the shared buffer 'buf' (padded by spad).  IN_SMEM / OUT_SMEM say that gld / gst touch 'buf'
+// themselves.  Ends with a barrier.
+template <int LOGN, bool IN_SMEM, bool OUT_SMEM, int P = 0, class LD, class ST>
+__device__ __forceinline__ void row_fft(float sign, const float2 *tw, float2 *buf, LD gld, ST gst)
+{
+    constexpr int NP = fft_npass(LOGN);
+    constexpr bool first = P == 0, last = P == NP - 1;
+    constexpr bool src_smem = first ? IN_SMEM : true, dst_smem = last ? OUT_SMEM : true;
+    constexpr bool inplace = (src_smem && dst_smem) || NP == 1;
+    auto sld = [&](int i) { return buf[spad(i)]; };
+    auto sst = [&](int i, float2 v) { buf[spad(i)] = v; };
+    if constexpr (first && last) stockham_pass<LOGN, P>(sign, tw, gld, gst, inplace);
+    else if constexpr (first) stockham_pass<LOGN, P>(sign, tw, gld, sst, inplace);
+    else if constexpr (last) stockham_pass<LOGN, P>(sign, tw, sld, gst, inplace);
+    else stockham_pass<LOGN, P>(sign, tw, sld, sst, inplace);
+    __syncthreads();
+    if constexpr (P + 1 < NP) row_fft<LOGN, IN_SMEM, OUT_SMEM, P + 1>(sign, tw, buf, gld, gst);
+}
+
+#define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L)))
+
+// In-place FFT of 'rows' consecutive rows of 2^LOGN points, times 'scale'.
+template <int LOGN>
+__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, int rows, float sign, const float2 *__restrict__ tw,
+                                            float scale)
 {
     extern __shared__ float2 sm[];
-    const int n = 1 << logn;
-    float2 *a = sm, *b = sm + n, *c = sm + 2 * n;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        float2 *d = data + (size_t)row * n;
-        const float2 *h = Ht + (size_t)row * n;
-        row_fft(logn, -1.0f, tw, a, b, [&](int i) { return d[i]; },
-                [&](int i, float2 v) { c[i] = cmul(v, __ldg(h + i)); });
-        row_fft(logn, +1.0f, tw, a, b, [&](int i) { return c[i]; }, [&](int i, float2 v) { d[i] = v; });
+        float2 *d = data + ((size_t)row << LOGN);
+        row_fft<LOGN, false, false>(sign, tw, sm, [&](int i) { return d[i]; },
+                                    [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
     }
 }
 
-// ASM pass 3: inverse FFT of the rows that hold the window, cropped into the output field.
-__global__ void __launch_bounds__(FFT_THREADS) k_asm_rows_out(const float2 *__restrict__ data, float2 *__restrict__ out,
-                                                              int logn, int W, int H, int ox, int oy,
-                                                              const float2 *__restrict__ tw)
+// The ASM's 2-D transforms skip the zero padding: only the H rows of the window are transformed
+// along x, kept compact (H rows of n_x), transposed to n_x columns of H, and each column is
+// zero-extended to n_y as it is loaded and only its window rows are stored after the inverse
+// transform; the rows outside the window are never written nor read.
+
+// ASM pass 1: forward FFT along x of the window's rows, zero-padded to 2^LOGN: out[y][k] for
+// y < rows (the H rows of each of the fields, one field after the other), from in[y][k - ox]
+// inside the window and 0 outside it.
+template <int LOGN>
+__global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, float2 *__restrict__ out, int W,
+                                               int rows, int ox, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    const int n = 1 << logn;
-    for (int y = blockIdx.x; y < H; y += gridDim.x) {
-        const float2 *d = data + (size_t)(y + oy) * n;
-        float2 *dst = out + (size_t)y * W;
-        row_fft(logn, +1.0f, tw, sm, sm + n, [&](int i) { return d[i]; },
-                [&](int i, float2 v) {
-                    const int x = i - ox;
-                    if (x >= 0 && x < W) dst[x] = v;
-                });
+    for (int y = blockIdx.x; y < rows; y += gridDim.x) {
+        float2 *d = out + ((size_t)y << LOGN);
+        const float2 *src = in + (size_t)y * W;
+        row_fft<LOGN, false, false>(-1.0f, tw, sm,
+                                    [&](int i) {
+                                        const int x = i - ox;
+                                        const float2 a = __ldg(src + min(max(x, 0), W - 1));   // in bounds
+                                        return (x >= 0 && x < W) ? a : make_float2(0.0f, 0.0f);
+                                    },
+                                    [&](int i, float2 v) { d[i] = v; });
     }
 }
 
-// out[x][y] = in[y][x], in is h x w
+// ASM pass 2, on the transposed spectra (per field, one compact column of H values per spatial
+// frequency fx, 'rows' of them): zero-extension to 2^LOGN rows (the window at rows
+// oy .. oy + H - 1), forward FFT into shared memory, multiplication by the transfer function's
+// row (scale folded in), inverse FFT, and the window's rows stored back in place.  A block takes
+// one fx for all nf fields in turn, so that the transfer function's row is read from memory once.
+template <int LOGN>
+__global__ void FFT_BOUNDS(LOGN) k_asm_rows_conv(float2 *data, int rows, int H, int oy, int nf,
+                                                 const float2 *__restrict__ Ht, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    for (int it = blockIdx.x; it < rows * nf; it += gridDim.x) {
+        const int row = it / nf, f = it - row * nf;
+        float2 *d = data + ((size_t)f * rows + row) * H;
+        const float2 *h = Ht + ((size_t)row << LOGN);
+        row_fft<LOGN, false, true>(-1.0f, tw, sm,
+                                   [&](int i) {
+                                       const int y = i - oy;
+                                       const float2 a = d[min(max(y, 0), H - 1)];                // in bounds
+                                       return (y >= 0 && y < H) ? a : make_float2(0.0f, 0.0f);
+                                   },
+                                   [&](int i, float2 v) { sm[spad(i)] = v; });
+        for (int i = threadIdx.x; i < (1 << LOGN); i += blockDim.x) sm[spad(i)] = cmul(sm[spad(i)], __ldg(h + i));
+        __syncthreads();
+        row_fft<LOGN, true, false>(+1.0f, tw, sm, [&](int i) { return sm[spad(i)]; },
+                                   [&](int i, float2 v) {
+                                       const int y = i - oy;
+                                       if (y >= 0 && y < H) d[y] = v;
+                                   });
+    }
+}
+
+// ASM pass 3: inverse FFT along x of the compact rows (H per field), cropped into the output
+// fields.
+template <int LOGN>
+__global__ void FFT_BOUNDS(LOGN) k_asm_rows_out(const float2 *__restrict__ data, float2 *__restrict__ out, int W,
+                                                int rows, int ox, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    for (int y = blockIdx.x; y < rows; y += gridDim.x) {
+        const float2 *d = data + ((size_t)y << LOGN);
+        float2 *dst = out + (size_t)y * W;
+        row_fft<LOGN, false, false>(+1.0f, tw, sm, [&](int i) { return d[i]; },
+                                    [&](int i, float2 v) {
+                                        const int x = i - ox;
+                                        if (x >= 0 && x < W) dst[x] = v;
+                                    });
+    }
+}
+
+// calls f(std::integral_constant<int, logn>) for logn in [1, FFT_MAX_LOG]
+template <class F>
+cudaError_t with_logn(int logn, F f)
+{
+    switch (logn) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 7: return f(std::integral_constant<int, 7>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    case 10: return f(std::integral_constant<int, 10>{});
+    case 11: return f(std::integral_constant<int, 11>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    case 13: return f(std::integral_constant<int, 13>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// out[x][y] = in[y][x], in is h x w; blockIdx.z selects one of several w x h matrices stored
+// one after the other
 __global__ void k_transpose(const float2 *__restrict__ in, float2 *__restrict__ out, int w, int h)
 {
     __shared__ float2 tile[32][33];
+    in += (size_t)blockIdx.z * w * h;
+    out += (size_t)blockIdx.z * w * h;
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int x = bx + threadIdx.x, y = by + k;
@@ -277,25 +345,35 @@ __global__ void k_arg(const float2 *__restrict__ r, float *__restrict__ phi, siz
 
 // exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) on the padded grid (FFT order), times 'scale',
 // stored transposed: Ht[ix][iy]
-__global__ void k_transfer(float2 *Hf, int Wp, int Hp, double pitch, double lambda, double z, float scale)
+__global__ void k_transfer(float2 *Hf, int Wp, int Hp, float2 fx_unit, float2 fy_unit, float2 inv_lambda2, float2 zdist,
+                           float scale)
 {
-    const size_t n = (size_t)Wp * Hp;
-    const double il2 = 1.0 / (lambda * lambda);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int iy = (int)(i % Hp), ix = (int)(i / Hp);
-        const double fx = (double)(ix < Wp / 2 ? ix : ix - Wp) / (Wp * pitch);
-        const double fy = (double)(iy < Hp / 2 ? iy : iy - Hp) / (Hp * pitch);
-        const double a = il2 - fx * fx - fy * fy;
+    // double-float arithmetic (~48-bit significands): the phase runs to ~1e5 turns and its
+    // fraction must hold ~1e-7
+    const int ix = blockIdx.y;                               // one transposed row per fx
+    const df fx = mul_f(mkdf(fx_unit.x, fx_unit.y), (float)(ix < Wp / 2 ? ix : ix - Wp));
+    const df base = mkdf(inv_lambda2.x, inv_lambda2.y) - fx * fx;
+    const df fyu = mkdf(fy_unit.x, fy_unit.y), z = mkdf(zdist.x, zdist.y);
+    float2 *row = Hf + (size_t)ix * Hp;
+    for (int iy = blockIdx.x * blockDim.x + threadIdx.x; iy < Hp; iy += gridDim.x * blockDim.x) {
+        const df fy = mul_f(fyu, (float)(iy < Hp / 2 ? iy : iy - Hp));
+        const df a = base - fy * fy;
         float2 v = make_float2(0.0f, 0.0f);
-        if (a > 0.0) {
-            const double turns = z * sqrt(a);
-            const float f = (float)(turns - floor(turns));
-            float s, c;
-            sincospif(2.0f * f, &s, &c);
-            v = make_float2(c * scale, s * scale);
+        if (a.hi > 0.0f) {
+            const float f = RealOps<df>::frac_f(z * df_sqrt(a));
+            float sn, cs;
+            sincospif(2.0f * f, &sn, &cs);
+            v = make_float2(cs * scale, sn * scale);
         }
-        Hf[i] = v;
+        row[iy] = v;
     }
+}
+
+// a double as a double-float pair (head, tail)
+float2 to_df(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
 }
 
 int ilog2(int n)
@@ -316,13 +394,20 @@ int grid_for(size_t n)
 cudaError_t fft2d(float2 *A, float2 *B, int nx, int ny, const float2 *twx, const float2 *twy, float sign, float scale,
                   cudaStream_t s)
 {
-    const int lx = ilog2(nx), ly = ilog2(ny);
     const dim3 tb(32, 8);
-    k_fft_rows<<<std::min(ny, 152 * 8), fft_threads(nx), 2 * sizeof(float2) * nx, s>>>(
-        A, lx, ny, sign, twx, 1.0f);
+    cudaError_t e = with_logn(ilog2(nx), [&](auto L) {
+        constexpr int l = decltype(L)::value;
+        k_fft_rows<l><<<std::min(ny, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(A, ny, sign, twx, 1.0f);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
-    k_fft_rows<<<std::min(nx, 152 * 8), fft_threads(ny), 2 * sizeof(float2) * ny, s>>>(
-        B, ly, nx, sign, twy, scale);
+    e = with_logn(ilog2(ny), [&](auto L) {
+        constexpr int l = decltype(L)::value;
+        k_fft_rows<l><<<std::min(nx, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, sign, twy, scale);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
     k_transpose<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, A, ny, nx);
     return cudaGetLastError();
 }
@@ -331,13 +416,20 @@ cudaError_t fft_setup()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    const int smem = (int)(3 * sizeof(float2)) << FFT_MAX_LOG;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_in, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_asm_rows_out, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) done = true;
-    return e;
+    for (int l = 1; l <= FFT_MAX_LOG; ++l) {
+        cudaError_t e = with_logn(l, [&](auto L) {
+            constexpr int ll = decltype(L)::value;
+            const int smem = fft_smem_bytes(1 << ll);
+            cudaError_t r = cudaFuncSetAttribute(k_fft_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_in<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_conv<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_out<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+    }
+    done = true;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -396,20 +488,37 @@ struct AsmPlan {
     float2 *A, *B, *twx, *twy;
 };
 
-cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, const float2 *Ht, cudaStream_t s)
+// nf fields of one wavelength (consecutive W x H fields of 'in' and 'out'; P.A and P.B hold
+// nf x Wp x H each)
+cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, const float2 *Ht, cudaStream_t s)
 {
-    // rows of the padded field -> transpose -> per-frequency rows: FFT, transfer, inverse FFT
-    // -> transpose -> inverse FFT of the window's rows, cropped
+    // the window's rows along x (H x Wp per field, compact) -> transpose (Wp x H) -> per-frequency
+    // columns zero-extended to Hp: FFT, transfer, inverse FFT, window rows kept -> transpose
+    // (H x Wp) -> inverse FFT along x, cropped
     const dim3 tb(32, 8);
-    k_asm_rows_in<<<std::min(P.Hp, 152 * 8), fft_threads(P.Wp), 2 * sizeof(float2) * P.Wp,
-                    s>>>(in, P.A, P.lx, P.Hp, P.W, P.H, P.ox, P.oy, P.twx);
-    k_transpose<<<dim3((P.Wp + 31) / 32, (P.Hp + 31) / 32), tb, 0, s>>>(P.A, P.B, P.Wp, P.Hp);
-    k_asm_rows_conv<<<std::min(P.Wp, 152 * 8), fft_threads(P.Hp), 3 * sizeof(float2) * P.Hp, s>>>(P.B, P.ly, P.Wp,
-                                                                                                   Ht, P.twy);
-    k_transpose<<<dim3((P.Hp + 31) / 32, (P.Wp + 31) / 32), tb, 0, s>>>(P.B, P.A, P.Hp, P.Wp);
-    k_asm_rows_out<<<std::min(P.H, 152 * 8), fft_threads(P.Wp), 2 * sizeof(float2) * P.Wp,
-                     s>>>(P.A, out, P.lx, P.W, P.H, P.ox, P.oy, P.twx);
-    return cudaGetLastError();
+    const int rows = nf * P.H;
+    cudaError_t e = with_logn(P.lx, [&](auto L) {
+        constexpr int l = decltype(L)::value;
+        k_asm_rows_in<l><<<std::min(rows, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(in, P.A, P.W, rows,
+                                                                                                       P.ox, P.twx);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    k_transpose<<<dim3((P.Wp + 31) / 32, (P.H + 31) / 32, nf), tb, 0, s>>>(P.A, P.B, P.Wp, P.H);
+    e = with_logn(P.ly, [&](auto L) {
+        constexpr int l = decltype(L)::value;
+        k_asm_rows_conv<l><<<std::min(P.Wp * nf, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
+            P.B, P.Wp, P.H, P.oy, nf, Ht, P.twy);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    k_transpose<<<dim3((P.H + 31) / 32, (P.Wp + 31) / 32, nf), tb, 0, s>>>(P.B, P.A, P.H, P.Wp);
+    return with_logn(P.lx, [&](auto L) {
+        constexpr int l = decltype(L)::value;
+        k_asm_rows_out<l><<<std::min(rows, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W,
+                                                                                                        rows, P.ox, P.twx);
+        return cudaGetLastError();
+    });
 }
 
 bool asm_sizes(int W, int H, AsmPlan &P)
@@ -439,49 +548,71 @@ __global__ void k_phase_field(const float *__restrict__ phi, float2 *__restrict_
     }
 }
 
-// per-block partial sums (double) of <A, T> = sum conj(A) T and <A, A>
+// Reductions: each thread sums its elements in float in runs of RED_RUN, the runs and the
+// block's threads in double (a fixed order: the result does not depend on timing).
+constexpr int RED_RUN = 16;
+
+// tree sum of v over the block's RED_THREADS threads (in place in the shared array)
+__device__ __forceinline__ double block_sum(double *sh, double v)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// per-block partial sums of <A, T> = sum conj(A) T and <A, A>
 __global__ void __launch_bounds__(RED_THREADS) k_dots(const float2 *__restrict__ A, const float2 *__restrict__ T, size_t n,
                                                       double *__restrict__ part)
 {
-    __shared__ double sre[RED_THREADS], sim[RED_THREADS], saa[RED_THREADS];
+    __shared__ double sh[RED_THREADS];
     double re = 0.0, im = 0.0, aa = 0.0;
+    float fre = 0.0f, fim = 0.0f, faa = 0.0f;
+    int c = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float2 a = A[i], t = T[i];
-        re += (double)a.x * t.x + (double)a.y * t.y;
-        im += (double)a.x * t.y - (double)a.y * t.x;
-        aa += (double)a.x * a.x + (double)a.y * a.y;
-    }
-    sre[threadIdx.x] = re;
-    sim[threadIdx.x] = im;
-    saa[threadIdx.x] = aa;
-    __syncthreads();
-    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            sre[threadIdx.x] += sre[threadIdx.x + o];
-            sim[threadIdx.x] += sim[threadIdx.x + o];
-            saa[threadIdx.x] += saa[threadIdx.x + o];
+        const float2 a = __ldg(A + i), t = __ldg(T + i);
+        fre += a.x * t.x + a.y * t.y;
+        fim += a.x * t.y - a.y * t.x;
+        faa += a.x * a.x + a.y * a.y;
+        if (++c == RED_RUN) {
+            re += fre; im += fim; aa += faa;
+            fre = fim = faa = 0.0f;
+            c = 0;
         }
-        __syncthreads();
     }
+    re += fre; im += fim; aa += faa;
+    re = block_sum(sh, re);
+    im = block_sum(sh, im);
+    aa = block_sum(sh, aa);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x] = sre[0];
-        part[3 * blockIdx.x + 1] = sim[0];
-        part[3 * blockIdx.x + 2] = saa[0];
+        part[3 * blockIdx.x] = re;
+        part[3 * blockIdx.x + 1] = im;
+        part[3 * blockIdx.x + 2] = aa;
     }
 }
 
-// s = <A, T> / <A, A>, from the partial sums in a fixed order
-__global__ void k_scale(const double *__restrict__ part, int nb, double *__restrict__ sc)
+// s = <A, T> / <A, A> from the nb partial sums (one block)
+__global__ void __launch_bounds__(RED_THREADS) k_scale(const double *__restrict__ part, int nb, double *__restrict__ sc)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[RED_THREADS];
     double re = 0.0, im = 0.0, aa = 0.0;
-    for (int b = 0; b < nb; ++b) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         re += part[3 * b];
         im += part[3 * b + 1];
         aa += part[3 * b + 2];
     }
-    sc[0] = aa > 0.0 ? re / aa : 0.0;
-    sc[1] = aa > 0.0 ? im / aa : 0.0;
+    re = block_sum(sh, re);
+    im = block_sum(sh, im);
+    aa = block_sum(sh, aa);
+    if (threadIdx.x == 0) {
+        sc[0] = aa > 0.0 ? re / aa : 0.0;
+        sc[1] = aa > 0.0 ? im / aa : 0.0;
+    }
 }
 
 // V = conj(s) (s A - T), with per-block partial sums of |s A - T|^2
@@ -489,30 +620,34 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(const float2 *__restri
                                                           const double *__restrict__ sc, float2 *__restrict__ V, size_t n,
                                                           double *__restrict__ part)
 {
-    __shared__ double sl[RED_THREADS];
+    __shared__ double sh[RED_THREADS];
     const float sr = (float)sc[0], si = (float)sc[1];
     double l = 0.0;
+    float fl = 0.0f;
+    int c = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float2 a = A[i], t = T[i];
+        const float2 a = A[i], t = __ldg(T + i);
         const float rr = sr * a.x - si * a.y - t.x, ri = sr * a.y + si * a.x - t.y;
-        l += (double)rr * rr + (double)ri * ri;
+        fl += rr * rr + ri * ri;
+        if (++c == RED_RUN) {
+            l += fl;
+            fl = 0.0f;
+            c = 0;
+        }
         V[i] = make_float2(sr * rr + si * ri, sr * ri - si * rr);
     }
-    sl[threadIdx.x] = l;
-    __syncthreads();
-    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sl[threadIdx.x] += sl[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sl[0];
+    l = block_sum(sh, l + fl);
+    if (threadIdx.x == 0) part[blockIdx.x] = l;
 }
 
-__global__ void k_loss(const double *__restrict__ part, int nb, double *__restrict__ loss)
+// the loss from the nb partial sums (one block)
+__global__ void __launch_bounds__(RED_THREADS) k_loss(const double *__restrict__ part, int nb, double *__restrict__ loss)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[RED_THREADS];
     double l = 0.0;
-    for (int b = 0; b < nb; ++b) l += part[b];
-    *loss = l;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) l += part[b];
+    l = block_sum(sh, l);
+    if (threadIdx.x == 0) *loss = l;
 }
 
 // phi <- phi - lr dL/dphi, dL/dphi = -2 Im(u conj(G))
@@ -546,25 +681,31 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     OPT_TRY(fft_setup());
     cudaStream_t s = (cudaStream_t)stream;
     const size_t np = (size_t)Wp * Hp;
-    const size_t bytes = (2 + (size_t)n_lambda) * np * sizeof(float2) + (size_t)(Wp + Hp) * sizeof(float2);
+    const int KB = std::min(K, ASM_BATCH);                 // fields per launch group
+    const size_t nab = std::max(np, (size_t)KB * Wp * H);
+    const size_t bytes = (2 * nab + (size_t)n_lambda * np + (size_t)(Wp + Hp)) * sizeof(float2);
     char *buf = nullptr;
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
     P.A = (float2 *)buf;
-    P.B = P.A + np;
-    float2 *Hf = P.B + np;
+    P.B = P.A + nab;
+    float2 *Hf = P.B + nab;
     P.twx = Hf + (size_t)n_lambda * np;
     P.twy = P.twx + Wp;
     cudaError_t e = cudaSuccess;
     k_twiddles<<<(Wp + 255) / 256, 256, 0, s>>>(P.twx, Wp);
     k_twiddles<<<(Hp + 255) / 256, 256, 0, s>>>(P.twy, Hp);
     for (int l = 0; l < n_lambda; ++l)
-        k_transfer<<<grid_for(np), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, pitch, lambdas[l], z, 1.0f / (float)np);
+        k_transfer<<<dim3((Hp + 255) / 256, Wp), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, to_df(1.0 / (Wp * pitch)),
+                                                              to_df(1.0 / (Hp * pitch)),
+                                                              to_df(1.0 / (lambdas[l] * lambdas[l])), to_df(z),
+                                                              1.0f / (float)np);
     const float2 *in = (const float2 *)in_dev;
     float2 *out = (float2 *)out_dev;
-    for (int f = 0; f < n_lambda * K && e == cudaSuccess; ++f) {
-        const size_t fo = (size_t)f * W * H;
-        e = asm_field(P, in + fo, out + fo, Hf + (size_t)(f / K) * np, s);
-    }
+    for (int l = 0; l < n_lambda && e == cudaSuccess; ++l)
+        for (int k = 0; k < K && e == cudaSuccess; k += KB) {
+            const size_t fo = ((size_t)l * K + k) * W * H;
+            e = asm_field(P, in + fo, out + fo, std::min(KB, K - k), Hf + (size_t)l * np, s);
+        }
     cudaError_t e2 = cudaFreeAsync(buf, s);
     OPT_TRY(e);
     OPT_TRY(e2);
@@ -601,18 +742,20 @@ extern "C" hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, flo
     const float2 *T = (const float2 *)target_dev;
     k_twiddles<<<(P.Wp + 255) / 256, 256, 0, s>>>(P.twx, P.Wp);
     k_twiddles<<<(P.Hp + 255) / 256, 256, 0, s>>>(P.twy, P.Hp);
-    k_transfer<<<grid_for(np), 256, 0, s>>>(Hp_, P.Wp, P.Hp, pitch, lambda, z, 1.0f / (float)np);
-    k_transfer<<<grid_for(np), 256, 0, s>>>(Hm, P.Wp, P.Hp, pitch, lambda, -z, 1.0f / (float)np);
+    const dim3 tg((P.Hp + 255) / 256, P.Wp);
+    const float2 fxu = to_df(1.0 / (P.Wp * pitch)), fyu = to_df(1.0 / (P.Hp * pitch)), il2 = to_df(1.0 / (lambda * lambda));
+    k_transfer<<<tg, 256, 0, s>>>(Hp_, P.Wp, P.Hp, fxu, fyu, il2, to_df(z), 1.0f / (float)np);
+    k_transfer<<<tg, 256, 0, s>>>(Hm, P.Wp, P.Hp, fxu, fyu, il2, to_df(-z), 1.0f / (float)np);
     cudaError_t e = cudaGetLastError();
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         k_phase_field<<<grid_for(n), 256, 0, s>>>(phi_dev, U, n);
-        e = asm_field(P, U, Afield, Hp_, s);
+        e = asm_field(P, U, Afield, 1, Hp_, s);
         if (e != cudaSuccess) break;
         k_dots<<<RED_BLOCKS, RED_THREADS, 0, s>>>(Afield, T, n, part);
-        k_scale<<<1, 32, 0, s>>>(part, RED_BLOCKS, sc);
+        k_scale<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, sc);
         k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(Afield, T, sc, V, n, part);
-        k_loss<<<1, 32, 0, s>>>(part, RED_BLOCKS, dloss + it);
-        e = asm_field(P, V, V, Hm, s);
+        k_loss<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, dloss + it);
+        e = asm_field(P, V, V, 1, Hm, s);
         if (e != cudaSuccess) break;
         k_phase_step<<<grid_for(n), 256, 0, s>>>(phi_dev, U, V, n, lr);
         e = cudaGetLastError();

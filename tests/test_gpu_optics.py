@@ -54,7 +54,8 @@ def _field(rng, shape):
     return (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("W,H,K,z", [(300, 200, 2, 12e-3), (37, 5, 1, -3e-3), (1920, 1080, 1, 80e-3)])
+@pytest.mark.parametrize("W,H,K,z", [(300, 200, 2, 12e-3), (37, 5, 1, -3e-3), (40, 24, 11, 5e-3),
+                                       (1920, 1080, 1, 80e-3)])
 def test_asm_matches_the_oracle(ctx, wo, torch_cuda, W, H, K, z):
     torch = torch_cuda
     lams = (638e-9, 520e-9, 450e-9)
