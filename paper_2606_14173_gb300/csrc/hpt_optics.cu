@@ -5,7 +5,9 @@
 // one block (Stockham autosort: radix-16 passes in registers, the remainder radix first, the
 // first pass reading global memory and the last writing it in natural order, the passes in
 // between in place in one bank-padded shared buffer), a tiled transpose, the rows again, and
-// the transpose back.  The data are complex64; the twiddle factors are rounded from
+// the transpose back.  Work around the transforms is folded into them: the GRF spectrum is
+// generated as the first pass loads it and the phase taken as the last transpose stores it;
+// the ASM's zero padding is never stored (see asm_field).  The data are complex64; the twiddle factors are rounded from
 // double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
 // ~1e5 turns, is formed in double-float arithmetic before its fraction is taken.
 #include <algorithm>
@@ -200,6 +202,38 @@ __global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, int rows, float sign, 
     }
 }
 
+// GRF pass 1 (Eq. 4): for each spectrum row ky < ny, the unit-modulus random spectrum
+// exp(i xi) inside the elliptic passband 4 (kx^2 ny^2 + ky^2 nx^2) <= nx^2 ny^2 (integers, FFT
+// order) and 0 outside it, xi = 2 pi u24(Philox(ix, iy, m, 'GRF'; seed)), generated as the
+// first pass loads it, and its unnormalised inverse FFT along x.
+template <int LOGN>
+__global__ void FFT_BOUNDS(LOGN) k_grf_rows(float2 *out, int ny, unsigned m, unsigned seed_lo, unsigned seed_hi,
+                                            const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    constexpr int nx = 1 << LOGN;
+    const long long NX = nx, NY = ny;
+    for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
+        const long long ky = iy < ny / 2 ? iy : iy - ny;
+        const long long rest = NX * NX * NY * NY - 4 * ky * ky * NX * NX;
+        float2 *d = out + ((size_t)iy << LOGN);
+        row_fft<LOGN, false, false>(+1.0f, tw, sm,
+                                    [&](int ix) {
+                                        const long long kx = ix < nx / 2 ? ix : ix - nx;
+                                        float2 v = make_float2(0.0f, 0.0f);
+                                        if (4 * kx * kx * NY * NY <= rest) {
+                                            const uint4 o = philox(make_uint4((unsigned)ix, (unsigned)iy, m, GRF_TAG),
+                                                                   seed_lo, seed_hi);
+                                            float sn, cs;
+                                            sincospif(2.0f * u24(o.x), &sn, &cs);
+                                            v = make_float2(cs, sn);
+                                        }
+                                        return v;
+                                    },
+                                    [&](int i, float2 v) { d[i] = v; });
+    }
+}
+
 // The ASM's 2-D transforms skip the zero padding: only the H rows of the window are transformed
 // along x, kept compact (H rows of n_x), transposed to n_x columns of H, and each column is
 // zero-extended to n_y as it is loaded and only its window rows are stored after the inverse
@@ -316,30 +350,22 @@ __global__ void k_transpose(const float2 *__restrict__ in, float2 *__restrict__ 
     }
 }
 
-// Eq. 4: exp(i xi_m) on the circular passband, 0 elsewhere; [ny][nx] in FFT order
-__global__ void k_grf_spectrum(float2 *spec, int nx, int ny, unsigned m, unsigned seed_lo, unsigned seed_hi)
+// out[x][y] = arg(in[y][x]) (atan2f), in is h x w
+__global__ void k_transpose_arg(const float2 *__restrict__ in, float *__restrict__ out, int w, int h)
 {
-    const size_t n = (size_t)nx * ny;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % nx), iy = (int)(i / nx);
-        const long long kx = ix < nx / 2 ? ix : ix - nx, ky = iy < ny / 2 ? iy : iy - ny;
-        const long long NX = nx, NY = ny;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (4 * (kx * kx * NY * NY + ky * ky * NX * NX) <= NX * NX * NY * NY) {
-            const uint4 o = philox(make_uint4((unsigned)ix, (unsigned)iy, m, GRF_TAG), seed_lo, seed_hi);
-            float s, c;
-            sincospif(2.0f * u24(o.x), &s, &c);
-            v = make_float2(c, s);
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int x = bx + threadIdx.x, y = by + k;
+        if (x < w && y < h) {
+            const float2 v = in[(size_t)y * w + x];
+            tile[k][threadIdx.x] = atan2f(v.y, v.x);
         }
-        spec[i] = v;
     }
-}
-
-__global__ void k_arg(const float2 *__restrict__ r, float *__restrict__ phi, size_t n)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float2 v = r[i];
-        phi[i] = atan2f(v.y, v.x);
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int x = by + threadIdx.x, y = bx + k;
+        if (x < h && y < w) out[(size_t)y * h + x] = tile[threadIdx.x][k];
     }
 }
 
@@ -391,27 +417,6 @@ int grid_for(size_t n)
 }
 
 // 2-D FFT of A [ny][nx] in place, B as scratch of the same size
-cudaError_t fft2d(float2 *A, float2 *B, int nx, int ny, const float2 *twx, const float2 *twy, float sign, float scale,
-                  cudaStream_t s)
-{
-    const dim3 tb(32, 8);
-    cudaError_t e = with_logn(ilog2(nx), [&](auto L) {
-        constexpr int l = decltype(L)::value;
-        k_fft_rows<l><<<std::min(ny, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(A, ny, sign, twx, 1.0f);
-        return cudaGetLastError();
-    });
-    if (e != cudaSuccess) return e;
-    k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
-    e = with_logn(ilog2(ny), [&](auto L) {
-        constexpr int l = decltype(L)::value;
-        k_fft_rows<l><<<std::min(nx, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, sign, twy, scale);
-        return cudaGetLastError();
-    });
-    if (e != cudaSuccess) return e;
-    k_transpose<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, A, ny, nx);
-    return cudaGetLastError();
-}
-
 cudaError_t fft_setup()
 {
     static bool done = false;
@@ -421,6 +426,7 @@ cudaError_t fft_setup()
             constexpr int ll = decltype(L)::value;
             const int smem = fft_smem_bytes(1 << ll);
             cudaError_t r = cudaFuncSetAttribute(k_fft_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_grf_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_in<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_conv<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_out<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -465,14 +471,27 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     cudaError_t e = cudaSuccess;
     k_twiddles<<<(nx + 255) / 256, 256, 0, s>>>(twx, nx);
     k_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(twy, ny);
+    // per map: spectrum generated and transformed along x, transpose, transform along y, the
+    // phase taken as the transpose back writes it
+    const dim3 tb(32, 8);
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
-        k_grf_spectrum<<<grid_for(n), 256, 0, s>>>(A, nx, ny, (unsigned)(hologram_offset + k), (unsigned)phase_seed,
-                                                   (unsigned)(phase_seed >> 32));
-        e = fft2d(A, B, nx, ny, twx, twy, +1.0f, 1.0f, s);
-        if (e == cudaSuccess) {
-            k_arg<<<grid_for(n), 256, 0, s>>>(A, phi_dev + (size_t)k * n, n);
-            e = cudaGetLastError();
-        }
+        e = with_logn(ilog2(nx), [&](auto L) {
+            constexpr int l = decltype(L)::value;
+            k_grf_rows<l><<<std::min(ny, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
+                A, ny, (unsigned)(hologram_offset + k), (unsigned)phase_seed, (unsigned)(phase_seed >> 32), twx);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) break;
+        k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
+        e = with_logn(ilog2(ny), [&](auto L) {
+            constexpr int l = decltype(L)::value;
+            k_fft_rows<l><<<std::min(nx, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, +1.0f, twy,
+                                                                                                      1.0f);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) break;
+        k_transpose_arg<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, phi_dev + (size_t)k * n, ny, nx);
+        e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(buf, s);
     OPT_TRY(e);
