@@ -36,6 +36,9 @@ constexpr int FFT_THREADS = 512;
 #ifndef HPT_FFT_REGS
 #define HPT_FFT_REGS 64                  // registers per thread the row kernels are compiled for
 #endif
+#ifndef HPT_FFT_CONV_REGS
+#define HPT_FFT_CONV_REGS 64             // the same for the ASM's y pass (two transforms per row)
+#endif
 constexpr unsigned GRF_TAG = 0x47524600u;
 constexpr int ASM_BATCH = 8;             // fields of one wavelength propagated by one group of launches
 
@@ -100,10 +103,10 @@ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int fft_smem_bytes(int n) { return (n + n / 16 + 1) * (int)sizeof(float2); }
 // threads of a row's block: n / 16 (each holds 16 points of a pass), at least one warp
 __host__ __device__ constexpr int fft_threads(int n) { return n / 16 > 32 ? (n / 16 < FFT_THREADS ? n / 16 : FFT_THREADS) : 32; }
-// resident blocks per SM the row kernels are compiled for: HPT_FFT_REGS registers per thread
-__host__ __device__ constexpr int fft_minb(int n)
+// resident blocks per SM the row kernels are compiled for: 'regs' registers per thread
+__host__ __device__ constexpr int fft_minb(int n, int regs)
 {
-    return 65536 / (HPT_FFT_REGS * fft_threads(n)) < 1 ? 1 : (65536 / (HPT_FFT_REGS * fft_threads(n)) > 32 ? 32 : 65536 / (HPT_FFT_REGS * fft_threads(n)));
+    return 65536 / (regs * fft_threads(n)) < 1 ? 1 : (65536 / (regs * fft_threads(n)) > 32 ? 32 : 65536 / (regs * fft_threads(n)));
 }
 // radix of pass p of a 2^logn-point transform (the remainder radix first, then 16s), the number
 // of passes, and the span Ns of the sub-transforms pass p combines
@@ -187,7 +190,8 @@ __device__ __forceinline__ void row_fft(float sign, const float2 *tw, float2 *bu
     if constexpr (P + 1 < NP) row_fft<LOGN, IN_SMEM, OUT_SMEM, P + 1>(sign, tw, buf, gld, gst);
 }
 
-#define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L)))
+#define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_REGS))
+#define FFT_BOUNDS_CONV(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS))
 
 // In-place FFT of 'rows' consecutive rows of 2^LOGN points, times 'scale'.
 template <int LOGN>
@@ -195,7 +199,8 @@ __global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, int rows, float sign, 
                                             float scale)
 {
     extern __shared__ float2 sm[];
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    {
+        const int row = blockIdx.x;   // one row per block (no loop: nothing is kept across rows)
         float2 *d = data + ((size_t)row << LOGN);
         row_fft<LOGN, false, false>(sign, tw, sm, [&](int i) { return d[i]; },
                                     [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
@@ -213,7 +218,8 @@ __global__ void FFT_BOUNDS(LOGN) k_grf_rows(float2 *out, int ny, unsigned m, uns
     extern __shared__ float2 sm[];
     constexpr int nx = 1 << LOGN;
     const long long NX = nx, NY = ny;
-    for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
+    {
+        const int iy = blockIdx.x;    // one row per block
         const long long ky = iy < ny / 2 ? iy : iy - ny;
         const long long rest = NX * NX * NY * NY - 4 * ky * ky * NX * NX;
         float2 *d = out + ((size_t)iy << LOGN);
@@ -247,7 +253,8 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
                                                int rows, int ox, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    for (int y = blockIdx.x; y < rows; y += gridDim.x) {
+    {
+        const int y = blockIdx.x;     // one row per block
         float2 *d = out + ((size_t)y << LOGN);
         const float2 *src = in + (size_t)y * W;
         row_fft<LOGN, false, false>(-1.0f, tw, sm,
@@ -266,11 +273,12 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
 // row (scale folded in), inverse FFT, and the window's rows stored back in place.  A block takes
 // one fx for all nf fields in turn, so that the transfer function's row is read from memory once.
 template <int LOGN>
-__global__ void FFT_BOUNDS(LOGN) k_asm_rows_conv(float2 *data, int rows, int H, int oy, int nf,
+__global__ void FFT_BOUNDS_CONV(LOGN) k_asm_rows_conv(float2 *data, int rows, int H, int oy, int nf,
                                                  const float2 *__restrict__ Ht, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    for (int it = blockIdx.x; it < rows * nf; it += gridDim.x) {
+    {
+        const int it = blockIdx.x;    // one (frequency, field) per block
         const int row = it / nf, f = it - row * nf;
         float2 *d = data + ((size_t)f * rows + row) * H;
         const float2 *h = Ht + ((size_t)row << LOGN);
@@ -298,7 +306,8 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_out(const float2 *__restrict__ data,
                                                 int rows, int ox, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    for (int y = blockIdx.x; y < rows; y += gridDim.x) {
+    {
+        const int y = blockIdx.x;     // one row per block
         const float2 *d = data + ((size_t)y << LOGN);
         float2 *dst = out + (size_t)y * W;
         row_fft<LOGN, false, false>(+1.0f, tw, sm, [&](int i) { return d[i]; },
@@ -477,7 +486,7 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
         e = with_logn(ilog2(nx), [&](auto L) {
             constexpr int l = decltype(L)::value;
-            k_grf_rows<l><<<std::min(ny, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
+            k_grf_rows<l><<<ny, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
                 A, ny, (unsigned)(hologram_offset + k), (unsigned)phase_seed, (unsigned)(phase_seed >> 32), twx);
             return cudaGetLastError();
         });
@@ -485,7 +494,7 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
         k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
         e = with_logn(ilog2(ny), [&](auto L) {
             constexpr int l = decltype(L)::value;
-            k_fft_rows<l><<<std::min(nx, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, +1.0f, twy,
+            k_fft_rows<l><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, +1.0f, twy,
                                                                                                       1.0f);
             return cudaGetLastError();
         });
@@ -518,7 +527,7 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
     const int rows = nf * P.H;
     cudaError_t e = with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_in<l><<<std::min(rows, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(in, P.A, P.W, rows,
+        k_asm_rows_in<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(in, P.A, P.W, rows,
                                                                                                        P.ox, P.twx);
         return cudaGetLastError();
     });
@@ -526,7 +535,7 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
     k_transpose<<<dim3((P.Wp + 31) / 32, (P.H + 31) / 32, nf), tb, 0, s>>>(P.A, P.B, P.Wp, P.H);
     e = with_logn(P.ly, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_conv<l><<<std::min(P.Wp * nf, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
+        k_asm_rows_conv<l><<<P.Wp * nf, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
             P.B, P.Wp, P.H, P.oy, nf, Ht, P.twy);
         return cudaGetLastError();
     });
@@ -534,7 +543,7 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
     k_transpose<<<dim3((P.H + 31) / 32, (P.Wp + 31) / 32, nf), tb, 0, s>>>(P.B, P.A, P.H, P.Wp);
     return with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_out<l><<<std::min(rows, 152 * 8), fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W,
+        k_asm_rows_out<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W,
                                                                                                         rows, P.ox, P.twx);
         return cudaGetLastError();
     });
