@@ -49,7 +49,7 @@ FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "ho
 # the 1920x270 band of the 30-sphere scene (same wave size as the full 1080p frame) in one ncu
 # capture; the summary and its command are in profiles/k_trace_dram_band_1920x270.md.  Set to
 # None whenever k_trace changes until it is captured again.
-TRACE_DRAM_BYTES_PER_LAUNCH = 401.5e6
+TRACE_DRAM_BYTES_PER_LAUNCH = 401.2e6
 
 
 # name -> (description, scene factory, render factory)
