@@ -228,7 +228,8 @@ hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *
  * nx^2 ny^2), xi_m = 2 pi u24(Philox4x32-10(kx mod nx, ky mod ny, m, 0x47524600; phase_seed)),
  * and writes phi_m = arg r_m in radians, float [K][ny][nx], to phi_dev (caller-owned device
  * memory, 4 K nx ny bytes).  nx, ny: powers of two, 2 .. 8192.  Runs on 'stream' (NULL: the
- * legacy default stream); scratch is taken from the context.  The paper's own numbers for the
+ * legacy default stream); its scratch (16 nx ny bytes and the twiddle tables) comes from the
+ * device's stream-ordered pool and is released on the stream.  The paper's own numbers for the
  * grid are not given: the caller chooses it to cover the image points' hologram positions
  * (the field is periodic). */
 hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t hologram_offset, int32_t K,
@@ -241,7 +242,10 @@ hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t hologram_off
  * the next powers of two of at least 2W and 2H (centred at ((Wp - W)/2, (Hp - H)/2)), its
  * spectrum multiplied by exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) (0 where the root is
  * imaginary), transformed back and cropped to the original window.  lambdas: host array of
- * n_lambda wavelengths (m).  Wp, Hp <= 8192.  Asynchronous on 'stream'. */
+ * n_lambda wavelengths (m).  Wp, Hp <= 8192.  Asynchronous on 'stream'.  The zero padding is
+ * never stored: the scratch, from the device's stream-ordered pool and released on the
+ * stream, is 8 (2 max(Wp Hp, min(K, 8) Wp H) + n_lambda Wp Hp) bytes (the K fields of a
+ * wavelength go through in groups of up to 8). */
 hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, int32_t W, int32_t H,
                              int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
                              void *stream);
@@ -254,7 +258,8 @@ hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, in
  * dL/dphi = -2 Im(exp(i phi) conj(ASM_-z(conj(s) (s A - T)))).  The supplementary section with
  * the paper's optimiser is not available: plain gradient descent with a fixed step is the
  * reading.  losses: host array of iters doubles (L before each step) or NULL; when given the
- * call waits for the stream.  Reductions in double. */
+ * call waits for the stream.  Reductions: runs of 16 terms per thread in float, the rest in
+ * double, in a fixed order. */
 hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, float *phi_dev, int32_t W, int32_t H,
                             double lambda, double pitch, double z, int32_t iters, float lr, double *losses,
                             void *stream);
