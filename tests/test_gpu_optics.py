@@ -37,7 +37,8 @@ def _wrapped(a, b):
     return np.abs(np.angle(np.exp(1j * (np.asarray(a, np.float64) - np.asarray(b, np.float64)))))
 
 
-@pytest.mark.parametrize("nx,ny,K,off", [(512, 256, 3, 2), (64, 2048, 1, 0), (4096, 4096, 2, 5)])
+@pytest.mark.parametrize("nx,ny,K,off", [(512, 256, 3, 2), (64, 2048, 1, 0), (4096, 4096, 2, 5), (8192, 64, 1, 1),
+                                           (2, 8, 2, 0)])
 def test_grf_maps_match_the_oracle(ctx, wo, nx, ny, K, off):
     p = 6.4e-6
     phi = ctx.grf_build(7, K, nx, ny, p, hologram_offset=off)
@@ -55,7 +56,7 @@ def _field(rng, shape):
 
 
 @pytest.mark.parametrize("W,H,K,z", [(300, 200, 2, 12e-3), (37, 5, 1, -3e-3), (40, 24, 11, 5e-3),
-                                       (1920, 1080, 1, 80e-3)])
+                                       (4000, 6, 1, 2e-3), (1, 1, 2, 1e-3), (1920, 1080, 1, 80e-3)])
 def test_asm_matches_the_oracle(ctx, wo, torch_cuda, W, H, K, z):
     torch = torch_cuda
     lams = (638e-9, 520e-9, 450e-9)
