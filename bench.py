@@ -233,23 +233,33 @@ def serve(ctx, hpt, S, requests, rate, seed):
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, len(requests))
     torch.cuda.synchronize()
-    ids, t0 = [], time.perf_counter()
+    ids, done, rejected, t0 = [], [], 0, time.perf_counter()
     t_next = t0
     for (sid, r, prec, out), g in zip(requests, gaps):
         t_next += g
         dt = t_next - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        ids.append(ctx.submit(sid, r, out, precision=prec))
+        try:
+            ids.append(ctx.submit(sid, r, out, precision=prec))
+            done.append(r)
+        except hpt.HptError as e:
+            if e.status != -5:           # only HPT_ERR_BUSY (the bounded queue is full) is expected
+                raise
+            rejected += 1
     for i in ids:
         ctx.wait(i, 600000)
+    if not ids:
+        return {"requests": len(requests), "rejected": rejected, "offered_rate_per_s": rate}
     times = np.array([ctx.request_times(i) for i in ids]) / 1e6
     lat = times[:, 2] - times[:, 0]
     span = times[:, 2].max() - times[:, 0].min()
-    holos = sum(r.K for _, r, _, _ in requests)
-    return {"requests": len(ids), "offered_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+    holos = sum(r.K for r in done)
+    return {"requests": len(requests), "rejected": rejected, "offered_rate_per_s": rate,
+            "completed_rate_per_s": len(ids) / span, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s": float(np.mean(times[:, 1] - times[:, 0])),
-            "holograms_per_s": holos / span, "path_samples_per_s": sum(r.path_samples() for _, r, _, _ in requests) / span,
+            "p99_queue_s": float(np.percentile(times[:, 1] - times[:, 0], 99)),
+            "holograms_per_s": holos / span, "path_samples_per_s": sum(r.path_samples() for r in done) / span,
             "span_s": float(span)}
 
 
@@ -316,20 +326,13 @@ def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
     }
 
 
-def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
-    """(a) headline requests (1080p RGB 64 spp depth 4 K=8) at 2 req/s, near the device's capacity;
-    (b) a mixed request stream at 40 req/s following the serving recipe (poses, focal depths,
-    SLM sizes, spp, K, scenes), scaled to 512x512 and 1920x1080 SLMs and spp <= 64 so that it ends
-    in seconds."""
-    rng = np.random.default_rng(4242)
-    head = [(sid_cfg1, S.config2_render(seed=10 + k), hpt.PREC_DF32, None) for k in range(6)]
-    head = [(sid, r, prec, hpt.alloc_output(r)) for sid, r, prec, _ in head]
-    a = serve(ctx, hpt, S, head, 2.0, 7)
-    a["workload"] = "6 requests of the headline render (1920x1080 RGB, 64 spp, depth 4, K=8), Poisson 2 req/s"
-    del head
-    mix = []
+def _mixed_requests(hpt, S, sid_cfg1, sid_cfg0, n, seed):
+    """n requests following the serving recipe (scenes, poses, focal depths, SLM sizes, spp, K),
+    scaled to 512x512 and 1920x1080 SLMs and spp <= 64 so that a stream ends in seconds."""
+    rng = np.random.default_rng(seed)
     z_med = {sid_cfg0: 7.5e-3, sid_cfg1: 17.5e-3}
-    for k in range(24):
+    mix = []
+    for k in range(n):
         sid = sid_cfg1 if rng.random() < 0.6 else sid_cfg0
         big = rng.random() < 0.4
         W, H = (1920, 1080) if big else (512, 512)
@@ -343,10 +346,45 @@ def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
             r = S.config0_render(W=W, H=H, spp=spp, K=K, seed=100 + k, pitch=6.4e-6,
                                  T=_pose_T(dx * 0.1, dy * 0.1, 0.0))
         mix.append((sid, r, hpt.PREC_DF32, hpt.alloc_output(r)))
-    b = serve(ctx, hpt, S, mix, 40.0, 8)
-    b["workload"] = ("24 requests, Poisson 40 req/s: scenes cfg1 (60%) / cfg0, SLM 512x512 or 1920x1080, spp in "
-                     "{16,32,64}, K in {1,4,8}, eye offsets U[-5,5] mm, focal depth U[5,30] mm")
-    return {"headline_requests": a, "mixed_stream": b}
+    return mix
+
+
+SWEEP_REQUESTS = 96
+MIX_DESC = ("Poisson arrivals; scenes cfg1 (60%) / cfg0, SLM 512x512 or 1920x1080, spp in {16,32,64}, "
+            "K in {1,4,8}, eye offsets U[-5,5] mm, focal depth U[5,30] mm")
+
+
+def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
+    """(a) headline requests (1080p RGB 64 spp depth 4 K=8) at 2 req/s, near the device's capacity;
+    (b) a mixed request stream at 40 req/s (unbounded queue); (c) the same mix with bounded
+    admission (8 requests on the device, 8 waiting; a submission beyond that is rejected and
+    counted) at increasing offered rates: the highest rate sustained is the highest with no
+    rejection and a p99 wait for admission under 1 s."""
+    head = [(sid_cfg1, S.config2_render(seed=10 + k), hpt.PREC_DF32, None) for k in range(6)]
+    head = [(sid, r, prec, hpt.alloc_output(r)) for sid, r, prec, _ in head]
+    a = serve(ctx, hpt, S, head, 2.0, 7)
+    a["workload"] = "6 requests of the headline render (1920x1080 RGB, 64 spp, depth 4, K=8), Poisson 2 req/s"
+    del head
+    b = serve(ctx, hpt, S, _mixed_requests(hpt, S, sid_cfg1, sid_cfg0, 24, 4242), 40.0, 8)
+    b["workload"] = "24 requests at 40 req/s, " + MIX_DESC
+    ctx.sync()
+    bounded = hpt.Context(ctx.device, max_inflight=8, max_queue=8)
+    sweep, best = [], 0.0
+    try:
+        s1, s0 = bounded.upload_scene(S.config1_scene()), bounded.upload_scene(S.config0_scene())
+        reqs = _mixed_requests(hpt, S, s1, s0, SWEEP_REQUESTS, 5000)     # the same stream at every rate
+        for k, rate in enumerate((10.0, 15.0, 20.0, 25.0, 30.0, 40.0)):
+            res = serve(bounded, hpt, S, reqs, rate, 9 + k)
+            sweep.append(res)
+            if res["rejected"] == 0 and res.get("p99_queue_s", 1e9) <= 1.0:
+                best = max(best, rate)
+        del reqs
+        bounded.sync()
+    finally:
+        bounded.close()
+    return {"headline_requests": a, "mixed_stream": b,
+            "bounded_sweep": {"max_inflight": 8, "max_queue": 8, "requests_per_rate": SWEEP_REQUESTS, "workload": MIX_DESC,
+                              "rates": sweep, "max_sustained_rate_per_s": best}}
 
 
 def run_reference(args):

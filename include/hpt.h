@@ -70,6 +70,9 @@ typedef struct {
                                    the free HBM at creation                                   */
     int32_t max_inflight;       /* serving: requests admitted and not finished (0 -> 8)       */
     int32_t flags;              /* HPT_CTX_* bits                                              */
+    int32_t max_queue;          /* serving: requests waiting for admission before hpt_submit
+                                   answers HPT_ERR_BUSY (0 -> 4096)                            */
+    int32_t reserved;           /* 0                                                           */
 } hpt_ctx_desc;
 
 /* Scene description.  All arrays are host memory, read during hpt_scene_upload only.
@@ -307,7 +310,8 @@ hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, con
 /* ---- serving: continuous batching of render requests ---------------------------------- */
 /* Queue a request; the scheduler thread admits it when a slot and memory are free and runs
  * it concurrently with the requests already on the device.  out_dev is caller-owned and must
- * stay valid until the request completes. */
+ * stay valid until the request completes.  HPT_ERR_BUSY (nothing queued) when max_queue
+ * requests already wait for admission. */
 hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                       void *out_dev, size_t out_bytes, uint64_t *req_id);
 /* *done = 1 when the request finished (its output is complete). */

@@ -398,6 +398,7 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     if (desc) {
         ctx->budget = desc->hbm_budget_bytes;
         if (desc->max_inflight > 0) ctx->max_inflight = desc->max_inflight;
+        if (desc->max_queue > 0) ctx->max_queue = (size_t)desc->max_queue;
     }
     if (ctx->budget == 0) {
         size_t fr = 0, tot = 0;

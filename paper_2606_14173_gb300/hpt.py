@@ -40,7 +40,8 @@ class HptError(RuntimeError):
 
 
 class CtxDesc(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_inflight", C.c_int32), ("flags", C.c_int32)]
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_inflight", C.c_int32), ("flags", C.c_int32),
+                ("max_queue", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Material(C.Structure):
@@ -157,10 +158,11 @@ def out_bytes(r) -> int:
 class Context:
     """One library context on one CUDA device (owns scenes and launch slots)."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, graphs: bool = True):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, graphs: bool = True,
+                 max_queue: int = 0):
         self.lib = load_library()
         self.h = C.c_void_p()
-        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0 if graphs else 1)
+        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0 if graphs else 1, max_queue, 0)
         _check(self.lib.hpt_create(C.byref(self.h), int(device), C.byref(desc)))
         self.device = device
 

@@ -49,6 +49,7 @@ int main(void) {
          offsetof(hpt_render_desc, grf_ny), HPT_PHASE_GRF);
   printf("%zu %zu %zu\n", sizeof(hpt_bake_desc), offsetof(hpt_bake_desc, spp), offsetof(hpt_bake_desc, seed));
   printf("%zu\n", offsetof(hpt_render_desc, omit_obliquity));
+  printf("%zu\n", offsetof(hpt_ctx_desc, max_queue));
   return 0;
 }
 '''
@@ -66,7 +67,7 @@ int main(void) {
            hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum"),
            hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF,
            C.sizeof(hpt.BakeDesc), hpt.BakeDesc.spp.offset, hpt.BakeDesc.seed.offset,
-           hpt.RenderDesc.omit_obliquity.offset]
+           hpt.RenderDesc.omit_obliquity.offset, hpt.CtxDesc.max_queue.offset]
     assert [int(x) for x in out] == got
 
 

@@ -113,3 +113,35 @@ def test_wait_timeout_and_unknown_ids(torch_cuda):
         assert e.value.status == -6
     finally:
         ctx.close()
+
+
+def test_bounded_queue_answers_busy(torch_cuda):
+    """With one request on the device and room for one waiting, a burst of four submissions
+    gets HPT_ERR_BUSY for at least one (nothing is queued for it); the accepted ones complete
+    with the fields of the same request traced alone, and the queue takes requests again once
+    it has drained."""
+    from paper_2606_14173_gb300 import hpt
+    ctx = hpt.Context(0, max_inflight=1, max_queue=1)
+    try:
+        sid = ctx.upload_scene(S.config1_scene())
+        r = S.config1_render(W=960, H=540, spp=64, K=8)
+        ref = hpt.alloc_output(r)
+        ctx.trace(sid, r, ref)
+        ctx.sync()
+        outs = [hpt.alloc_output(r) for _ in range(4)]
+        ids, busy = [], 0
+        for o in outs:
+            try:
+                ids.append((ctx.submit(sid, r, o), o))
+            except hpt.HptError as e:
+                assert e.status == -5, e
+                busy += 1
+        assert busy >= 1 and len(ids) >= 1
+        for i, o in ids:
+            ctx.wait(i, 120000)
+            assert torch_cuda.equal(o, ref)
+        i = ctx.submit(sid, r, outs[0])
+        ctx.wait(i, 120000)
+        assert torch_cuda.equal(outs[0], ref)
+    finally:
+        ctx.close()
