@@ -193,10 +193,9 @@ __device__ __forceinline__ void row_fft(float sign, const float2 *tw, float2 *bu
 #define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_REGS))
 #define FFT_BOUNDS_CONV(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS))
 
-// In-place FFT of 'rows' consecutive rows of 2^LOGN points, times 'scale'.
+// In-place FFT of row blockIdx.x of consecutive rows of 2^LOGN points, times 'scale'.
 template <int LOGN>
-__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, int rows, float sign, const float2 *__restrict__ tw,
-                                            float scale)
+__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, float sign, const float2 *__restrict__ tw, float scale)
 {
     extern __shared__ float2 sm[];
     {
@@ -246,11 +245,11 @@ __global__ void FFT_BOUNDS(LOGN) k_grf_rows(float2 *out, int ny, unsigned m, uns
 // transform; the rows outside the window are never written nor read.
 
 // ASM pass 1: forward FFT along x of the window's rows, zero-padded to 2^LOGN: out[y][k] for
-// y < rows (the H rows of each of the fields, one field after the other), from in[y][k - ox]
-// inside the window and 0 outside it.
+// row y = blockIdx.x (the H rows of each of the fields, one field after the other), from
+// in[y][k - ox] inside the window and 0 outside it.
 template <int LOGN>
-__global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, float2 *__restrict__ out, int W,
-                                               int rows, int ox, const float2 *__restrict__ tw)
+__global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, float2 *__restrict__ out, int W, int ox,
+                                               const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
     {
@@ -303,7 +302,7 @@ __global__ void FFT_BOUNDS_CONV(LOGN) k_asm_rows_conv(float2 *data, int rows, in
 // fields.
 template <int LOGN>
 __global__ void FFT_BOUNDS(LOGN) k_asm_rows_out(const float2 *__restrict__ data, float2 *__restrict__ out, int W,
-                                                int rows, int ox, const float2 *__restrict__ tw)
+                                                int ox, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
     {
@@ -468,7 +467,7 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     if (K < 1 || hologram_offset < 0) return internal_fail(HPT_ERR_INVALID_ARG, "K must be >= 1, hologram_offset >= 0");
     if (!pow2_in_range(nx) || !pow2_in_range(ny))
         return internal_fail(HPT_ERR_INVALID_ARG, "nx and ny must be powers of two in 2 .. 8192");
-    if (!(pitch > 0.0)) return internal_fail(HPT_ERR_INVALID_ARG, "pitch must be > 0");
+    if (!(pitch > 0.0) || !std::isfinite(pitch)) return internal_fail(HPT_ERR_INVALID_ARG, "pitch must be finite and > 0");
     OPT_TRY(cudaSetDevice(internal_ctx_device(ctx)));
     OPT_TRY(fft_setup());
     cudaStream_t s = (cudaStream_t)stream;
@@ -494,8 +493,7 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
         k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
         e = with_logn(ilog2(ny), [&](auto L) {
             constexpr int l = decltype(L)::value;
-            k_fft_rows<l><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, nx, +1.0f, twy,
-                                                                                                      1.0f);
+            k_fft_rows<l><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, +1.0f, twy, 1.0f);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) break;
@@ -527,8 +525,7 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
     const int rows = nf * P.H;
     cudaError_t e = with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_in<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(in, P.A, P.W, rows,
-                                                                                                       P.ox, P.twx);
+        k_asm_rows_in<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(in, P.A, P.W, P.ox, P.twx);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -543,8 +540,7 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
     k_transpose<<<dim3((P.H + 31) / 32, (P.Wp + 31) / 32, nf), tb, 0, s>>>(P.B, P.A, P.H, P.Wp);
     return with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_out<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W,
-                                                                                                        rows, P.ox, P.twx);
+        k_asm_rows_out<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W, P.ox, P.twx);
         return cudaGetLastError();
     });
 }
@@ -702,9 +698,11 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     AsmPlan P;
     if (!asm_sizes(W, H, P)) return internal_fail(HPT_ERR_UNSUPPORTED, "padded size above 8192 x 8192 (W, H <= 4096)");
     const int Wp = P.Wp, Hp = P.Hp;
-    if (!(pitch > 0.0)) return internal_fail(HPT_ERR_INVALID_ARG, "pitch must be > 0");
+    if (!(pitch > 0.0) || !std::isfinite(pitch) || !std::isfinite(z))
+        return internal_fail(HPT_ERR_INVALID_ARG, "pitch must be finite and > 0, z finite");
     for (int l = 0; l < n_lambda; ++l)
-        if (!(lambdas[l] > 0.0)) return internal_fail(HPT_ERR_INVALID_ARG, "wavelengths must be > 0");
+        if (!(lambdas[l] > 0.0) || !std::isfinite(lambdas[l]))
+            return internal_fail(HPT_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
     OPT_TRY(cudaSetDevice(internal_ctx_device(ctx)));
     OPT_TRY(fft_setup());
     cudaStream_t s = (cudaStream_t)stream;
@@ -748,7 +746,8 @@ extern "C" hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, flo
     if (st) return st;
     if (!target_dev || !phi_dev) return internal_fail(HPT_ERR_INVALID_ARG, "target_dev or phi_dev is NULL");
     if (W < 1 || H < 1 || iters < 0) return internal_fail(HPT_ERR_INVALID_ARG, "need W, H >= 1 and iters >= 0");
-    if (!(pitch > 0.0) || !(lambda > 0.0) || !std::isfinite(z) || !std::isfinite(lr))
+    if (!(pitch > 0.0) || !(lambda > 0.0) || !std::isfinite(pitch) || !std::isfinite(lambda) || !std::isfinite(z) ||
+        !std::isfinite(lr))
         return internal_fail(HPT_ERR_INVALID_ARG, "bad pitch, lambda, z or lr");
     AsmPlan P;
     if (!asm_sizes(W, H, P)) return internal_fail(HPT_ERR_UNSUPPORTED, "padded size above 8192 x 8192 (W, H <= 4096)");

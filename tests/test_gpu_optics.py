@@ -131,6 +131,11 @@ def test_invalid_arguments(ctx, torch_cuda):
     U = torch_cuda.zeros((1, 1, 8, 8), dtype=torch_cuda.complex64, device="cuda")
     with pytest.raises(hpt.HptError):
         ctx.asm_propagate(U, (-1.0,), 8e-6, 1e-3)
+    for lam, p, z in ((float("inf"), 8e-6, 1e-3), (520e-9, float("nan"), 1e-3), (520e-9, 8e-6, float("inf"))):
+        with pytest.raises(hpt.HptError):
+            ctx.asm_propagate(U, (lam,), p, z)
+    with pytest.raises(hpt.HptError):
+        ctx.grf_build(1, 1, 64, 64, float("inf"))
     ctx.sync()
 
 
