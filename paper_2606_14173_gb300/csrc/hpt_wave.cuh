@@ -238,6 +238,9 @@ __device__ __forceinline__ bool exact_hit(const DevScene &sc, int tri, const R3<
 #ifndef HPT_TRACE_MINB
 #define HPT_TRACE_MINB 8
 #endif
+#ifndef HPT_ACCUM_MINB
+#define HPT_ACCUM_MINB 1
+#endif
 
 template <class R, bool STATS>
 __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
@@ -737,7 +740,7 @@ __device__ __noinline__ float2 point_field(const DevJob *Jp, int lam, int px, in
 }
 
 template <class R>
-__global__ void __launch_bounds__(ACCUM_BLOCK) k_accum(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
+__global__ void __launch_bounds__(ACCUM_BLOCK, HPT_ACCUM_MINB) k_accum(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
                                                        SlotScratch *__restrict__ scr)
 {
     __shared__ int s_stack[TSTACK * ACCUM_BLOCK];
