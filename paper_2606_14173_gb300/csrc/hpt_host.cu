@@ -1200,7 +1200,9 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
     }
     J.out = (float2 *)ctx->host_out_dev;
     cudaStream_t s = (cudaStream_t)stream;
-    st = run_jobs(ctx, &J, 1, desc->precision, false, s);
+    // the device staging buffer is the context's, so the frame's captured graph is reused
+    st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, s)
+                                                  : run_jobs(ctx, &J, 1, desc->precision, false, s);
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out_dev, need, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));

@@ -44,6 +44,25 @@ def test_graph_replay_equals_direct_launches(torch_cuda):
         graphed.close()
 
 
+def test_trace_into_host_memory_equals_device_trace(torch_cuda):
+    """hpt_trace_host (the device trace into the context's staging buffer, then one copy to host
+    memory) gives the device trace's fields bit for bit: for repeated calls (a captured frame
+    replayed), with and without graphs, and after a larger request grows the staging buffer."""
+    from paper_2606_14173_gb300 import hpt
+    for graphs in (True, False):
+        ctx = hpt.Context(0, graphs=graphs)
+        try:
+            sid = ctx.upload_scene(S.config1_scene())
+            for W, H, K, seed in ((203, 117, 4, 1), (203, 117, 4, 2), (320, 180, 8, 3), (203, 117, 4, 1)):
+                r = S.config1_render(W=W, H=H, spp=8, K=K, seed=seed)
+                ref = _trace(ctx, sid, r, hpt.alloc_output(r))
+                host = np.empty(ref.shape, np.complex64)
+                ctx.trace_host(sid, r, host)
+                assert np.array_equal(host, ref), (graphs, W, H, K, seed)
+        finally:
+            ctx.close()
+
+
 def test_autotune_keeps_results(torch_cuda):
     from paper_2606_14173_gb300 import hpt
     ctx = hpt.Context(0)
