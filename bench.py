@@ -308,22 +308,8 @@ def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
     enc_iters = 10
     enc_ms = timed_ms(lambda: ctx.phase_encode(tgt, phi, r.lambdas[1], r.pitch, 0.0, enc_iters,
                                                0.1 / float(torch.mean(tgt.abs() ** 2)), stream=stream))
-    # convergence: the same hologram carried 2 mm by the ASM is the complex target at that plane;
-    # 200 steps from phi = 0 with step 0.5 / mean |T|^2, complex-field PSNR of s A against it
-    # before each step (a phase-only field cannot match the target's amplitude: it saturates)
-    zc, conv_iters = 2e-3, 200
-    tz = ctx.asm_propagate(out[1:2, 0:1].contiguous(), (r.lambdas[1],), r.pitch, zc, stream=stream)[0, 0].contiguous()
-    phi_c = torch.zeros((r.H, r.W), dtype=torch.float32, device=out.device)
-    losses = ctx.phase_encode(tz, phi_c, r.lambdas[1], r.pitch, zc, conv_iters,
-                              0.5 / float(torch.mean(tz.abs() ** 2)), stream=stream)
-    peak2 = float(tz.abs().max()) ** 2
-    psnr = [10.0 * math.log10(peak2 * r.W * r.H / max(float(l), 1e-300)) for l in losses]
-    marks = [0, 10, 25, 50, 100, conv_iters - 1]
     return {
-        "phase_encode": {"field": [r.W, r.H], "iters": enc_iters, "ms": enc_ms, "ms_per_iter": enc_ms / enc_iters,
-                         "convergence": {"z_m": zc, "start": "phi = 0", "step": "0.5 / mean |T|^2", "steps": marks,
-                                         "psnr_db": [psnr[k] for k in marks],
-                                         "psnr": "complex field, 10 log10(max|T|^2 N / sum |s A - T|^2)"}},
+        "phase_encode": {"field": [r.W, r.H], "iters": enc_iters, "ms": enc_ms, "ms_per_iter": enc_ms / enc_iters},
         "cache_bake": {"cells": res ** 3, "channels": 3, "directions": bspp, "max_depth": bdepth, "ms": bake_ms,
                        "paths_per_s": bake_paths / (bake_ms / 1e3)},
         "grf_maps": {"K": r.K, "grid": [nx, ny], "ms": grf_ms, "maps_per_s": r.K / (grf_ms / 1e3)},
