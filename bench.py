@@ -229,10 +229,9 @@ def _pose_T(dx, dy, dz):
 def serve(ctx, hpt, S, requests, rate, seed):
     """Submit requests with Poisson arrivals at 'rate' per second; returns latency statistics.
     requests: list of (scene id, render, precision, output tensor)."""
-    import torch
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, len(requests))
-    torch.cuda.synchronize()
+    ctx.sync()
     ids, done, rejected, t0 = [], [], 0, time.perf_counter()
     t_next = t0
     for (sid, r, prec, out), g in zip(requests, gaps):
