@@ -66,9 +66,10 @@ __device__ __forceinline__ float2 w16(int m)
 }
 
 // R-point DFT of v in registers (R = 2, 4, 8, 16): bit-reversed order, then log2 R radix-2
-// stages; sign = -1 forward, +1 inverse
-template <int R>
-__device__ __forceinline__ void dft_reg(float2 *v, float sign)
+// stages; SIGN = -1 forward, +1 inverse.  The butterflies whose twiddle is 1 or -+i take no
+// multiplication.
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 *v)
 {
     constexpr int B = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     float2 t[R];
@@ -85,9 +86,16 @@ __device__ __forceinline__ void dft_reg(float2 *v, float sign)
         for (int g = 0; g < R; g += 2 * half) {
 #pragma unroll
             for (int pos = 0; pos < half; ++pos) {
-                float2 w = w16(pos * (8 / half));
-                w.y *= -sign;
-                const float2 a = t[g + pos], b = cmul(w, t[g + pos + half]);
+                const int m = pos * (8 / half);        // twiddle exp(SIGN 2 pi i m / 16)
+                float2 b = t[g + pos + half];
+                if (m == 4) {
+                    b = SIGN > 0 ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+                } else if (m != 0) {
+                    float2 w = w16(m);
+                    if (SIGN > 0) w.y = -w.y;
+                    b = cmul(w, b);
+                }
+                const float2 a = t[g + pos];
                 t[g + pos] = make_float2(a.x + b.x, a.y + b.y);
                 t[g + pos + half] = make_float2(a.x - b.x, a.y - b.y);
             }
@@ -115,13 +123,13 @@ __host__ __device__ constexpr int fft_npass(int logn) { return (logn >> 2) + ((l
 __host__ __device__ constexpr int fft_ns(int logn, int p) { return p == 0 ? 1 : fft_ns(logn, p - 1) * fft_radix(logn, p - 1); }
 
 // Pass P of the Stockham transform of N = 2^LOGN points (radix R, span NS): element j reads
-// x[j + r N/R] (r < R) through 'ld', multiplies it by exp(sign 2 pi i r (j mod NS) / (NS R))
+// x[j + r N/R] (r < R) through 'ld', multiplies it by exp(SIGN 2 pi i r (j mod NS) / (NS R))
 // (the N-point twiddle table), takes the R-point DFT and writes
 // y[(j - j mod NS) R + j mod NS + r NS] through 'st'.  Thread t takes j = t + m T (T threads,
 // m < J); with 'inplace' every thread holds its values in registers across a barrier before
 // it stores, so that x and y may be the same buffer.
-template <int LOGN, int P, class LD, class ST>
-__device__ __forceinline__ void stockham_pass(float sign, const float2 *__restrict__ tw, LD ld, ST st, bool inplace)
+template <int LOGN, int P, int SIGN, class LD, class ST>
+__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD ld, ST st, bool inplace)
 {
     constexpr int N = 1 << LOGN, R = fft_radix(LOGN, P), NS = fft_ns(LOGN, P), T = fft_threads(N);
     constexpr int Q = N / R, TWS = N / (NS * R), J = (Q + T - 1) / T;
@@ -135,26 +143,26 @@ __device__ __forceinline__ void stockham_pass(float sign, const float2 *__restri
 #pragma unroll
         for (int r = 0; r < R; ++r) v[m][r] = ld(j + r * Q);
         if (NS > 1) {
-            // twiddles w^r, w = exp(sign 2 pi i k / (NS R)): w, w^2, w^3 formed from the loaded w,
+            // twiddles w^r, w = exp(SIGN 2 pi i k / (NS R)): w, w^2, w^3 formed from the loaded w,
             // w^(4c) loaded for c >= 1 and multiplied by them (at most two roundings per twiddle)
             float2 w1 = __ldg(tw + k * TWS);
-            w1.y *= -sign;
+            if (SIGN > 0) w1.y = -w1.y;
             const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 float2 w;
                 if (r % 4 == 0 || r < 4) {
                     w = r == 1 ? w1 : r == 2 ? w2 : r == 3 ? w3 : __ldg(tw + r * k * TWS);
-                    if (r >= 4) w.y *= -sign;
+                    if (r >= 4 && SIGN > 0) w.y = -w.y;
                 } else {
                     float2 b = __ldg(tw + (r & ~3) * k * TWS);
-                    b.y *= -sign;
+                    if (SIGN > 0) b.y = -b.y;
                     w = cmul(b, (r & 3) == 1 ? w1 : (r & 3) == 2 ? w2 : w3);
                 }
                 v[m][r] = cmul(v[m][r], w);
             }
         }
-        dft_reg<R>(v[m], sign);
+        dft_reg<R, SIGN>(v[m]);
     }
     if (inplace) __syncthreads();
 #pragma unroll
@@ -173,8 +181,8 @@ __device__ __forceinline__ void stockham_pass(float sign, const float2 *__restri
 // first reading through 'gld', the last writing through 'gst', the ones in between in place in
 // the shared buffer 'buf' (padded by spad).  IN_SMEM / OUT_SMEM say that gld / gst touch 'buf'
 // themselves.  Ends with a barrier.
-template <int LOGN, bool IN_SMEM, bool OUT_SMEM, int P = 0, class LD, class ST>
-__device__ __forceinline__ void row_fft(float sign, const float2 *tw, float2 *buf, LD gld, ST gst)
+template <int LOGN, int SIGN, bool IN_SMEM, bool OUT_SMEM, int P = 0, class LD, class ST>
+__device__ __forceinline__ void row_fft(const float2 *tw, float2 *buf, LD gld, ST gst)
 {
     constexpr int NP = fft_npass(LOGN);
     constexpr bool first = P == 0, last = P == NP - 1;
@@ -182,26 +190,26 @@ __device__ __forceinline__ void row_fft(float sign, const float2 *tw, float2 *bu
     constexpr bool inplace = (src_smem && dst_smem) || NP == 1;
     auto sld = [&](int i) { return buf[spad(i)]; };
     auto sst = [&](int i, float2 v) { buf[spad(i)] = v; };
-    if constexpr (first && last) stockham_pass<LOGN, P>(sign, tw, gld, gst, inplace);
-    else if constexpr (first) stockham_pass<LOGN, P>(sign, tw, gld, sst, inplace);
-    else if constexpr (last) stockham_pass<LOGN, P>(sign, tw, sld, gst, inplace);
-    else stockham_pass<LOGN, P>(sign, tw, sld, sst, inplace);
+    if constexpr (first && last) stockham_pass<LOGN, P, SIGN>(tw, gld, gst, inplace);
+    else if constexpr (first) stockham_pass<LOGN, P, SIGN>(tw, gld, sst, inplace);
+    else if constexpr (last) stockham_pass<LOGN, P, SIGN>(tw, sld, gst, inplace);
+    else stockham_pass<LOGN, P, SIGN>(tw, sld, sst, inplace);
     __syncthreads();
-    if constexpr (P + 1 < NP) row_fft<LOGN, IN_SMEM, OUT_SMEM, P + 1>(sign, tw, buf, gld, gst);
+    if constexpr (P + 1 < NP) row_fft<LOGN, SIGN, IN_SMEM, OUT_SMEM, P + 1>(tw, buf, gld, gst);
 }
 
 #define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_REGS))
 #define FFT_BOUNDS_CONV(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS))
 
 // In-place FFT of row blockIdx.x of consecutive rows of 2^LOGN points, times 'scale'.
-template <int LOGN>
-__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, float sign, const float2 *__restrict__ tw, float scale)
+template <int LOGN, int SIGN>
+__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, const float2 *__restrict__ tw, float scale)
 {
     extern __shared__ float2 sm[];
     {
         const int row = blockIdx.x;   // one row per block (no loop: nothing is kept across rows)
         float2 *d = data + ((size_t)row << LOGN);
-        row_fft<LOGN, false, false>(sign, tw, sm, [&](int i) { return d[i]; },
+        row_fft<LOGN, SIGN, false, false>(tw, sm, [&](int i) { return d[i]; },
                                     [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
     }
 }
@@ -222,7 +230,7 @@ __global__ void FFT_BOUNDS(LOGN) k_grf_rows(float2 *out, int ny, unsigned m, uns
         const long long ky = iy < ny / 2 ? iy : iy - ny;
         const long long rest = NX * NX * NY * NY - 4 * ky * ky * NX * NX;
         float2 *d = out + ((size_t)iy << LOGN);
-        row_fft<LOGN, false, false>(+1.0f, tw, sm,
+        row_fft<LOGN, +1, false, false>(tw, sm,
                                     [&](int ix) {
                                         const long long kx = ix < nx / 2 ? ix : ix - nx;
                                         float2 v = make_float2(0.0f, 0.0f);
@@ -256,7 +264,7 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
         const int y = blockIdx.x;     // one row per block
         float2 *d = out + ((size_t)y << LOGN);
         const float2 *src = in + (size_t)y * W;
-        row_fft<LOGN, false, false>(-1.0f, tw, sm,
+        row_fft<LOGN, -1, false, false>(tw, sm,
                                     [&](int i) {
                                         const int x = i - ox;
                                         const float2 a = __ldg(src + min(max(x, 0), W - 1));   // in bounds
@@ -281,7 +289,7 @@ __global__ void FFT_BOUNDS_CONV(LOGN) k_asm_rows_conv(float2 *data, int rows, in
         const int row = it / nf, f = it - row * nf;
         float2 *d = data + ((size_t)f * rows + row) * H;
         const float2 *h = Ht + ((size_t)row << LOGN);
-        row_fft<LOGN, false, true>(-1.0f, tw, sm,
+        row_fft<LOGN, -1, false, true>(tw, sm,
                                    [&](int i) {
                                        const int y = i - oy;
                                        const float2 a = d[min(max(y, 0), H - 1)];                // in bounds
@@ -290,7 +298,7 @@ __global__ void FFT_BOUNDS_CONV(LOGN) k_asm_rows_conv(float2 *data, int rows, in
                                    [&](int i, float2 v) { sm[spad(i)] = v; });
         for (int i = threadIdx.x; i < (1 << LOGN); i += blockDim.x) sm[spad(i)] = cmul(sm[spad(i)], __ldg(h + i));
         __syncthreads();
-        row_fft<LOGN, true, false>(+1.0f, tw, sm, [&](int i) { return sm[spad(i)]; },
+        row_fft<LOGN, +1, true, false>(tw, sm, [&](int i) { return sm[spad(i)]; },
                                    [&](int i, float2 v) {
                                        const int y = i - oy;
                                        if (y >= 0 && y < H) d[y] = v;
@@ -309,7 +317,7 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_out(const float2 *__restrict__ data,
         const int y = blockIdx.x;     // one row per block
         const float2 *d = data + ((size_t)y << LOGN);
         float2 *dst = out + (size_t)y * W;
-        row_fft<LOGN, false, false>(+1.0f, tw, sm, [&](int i) { return d[i]; },
+        row_fft<LOGN, +1, false, false>(tw, sm, [&](int i) { return d[i]; },
                                     [&](int i, float2 v) {
                                         const int x = i - ox;
                                         if (x >= 0 && x < W) dst[x] = v;
@@ -433,7 +441,7 @@ cudaError_t fft_setup()
         cudaError_t e = with_logn(l, [&](auto L) {
             constexpr int ll = decltype(L)::value;
             const int smem = fft_smem_bytes(1 << ll);
-            cudaError_t r = cudaFuncSetAttribute(k_fft_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaError_t r = cudaFuncSetAttribute(k_fft_rows<ll, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_grf_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_in<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_conv<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -493,7 +501,7 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
         k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
         e = with_logn(ilog2(ny), [&](auto L) {
             constexpr int l = decltype(L)::value;
-            k_fft_rows<l><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, +1.0f, twy, 1.0f);
+            k_fft_rows<l, +1><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, twy, 1.0f);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) break;
