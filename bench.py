@@ -42,13 +42,14 @@ def _hbm_peak():
 
 HBM_PEAK_GBS = _hbm_peak()
 ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
-# algorithmic FP32 work per counted event (see the design notes): two child-box slab tests per
-# node visit are counted as two box tests
+# algorithmic FP32 work per counted event: 20 flop per child-box slab test (two per node visit),
+# 30 per float ray-triangle test, 400 per coherent re-decision in double-float, 120 per
+# incoherent vertex (shadow ray or BSDF bounce), 25 per hologram of a path sample (phase + Kahan sum)
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
 # DRAM bytes (read + write) per k_trace launch, averaged over every k_trace launch of one frame of
 # the 1920x270 band of the 30-sphere scene (same wave size as the full 1080p frame) in one ncu
-# capture; the summary and its command are in profiles/k_trace_dram_band_1920x270.md.  Set to
-# None whenever k_trace changes until it is captured again.
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), copied here: the bench cannot read
+# hardware counters itself.  None whenever k_trace changed since that capture.
 TRACE_DRAM_BYTES_PER_LAUNCH = 401.2e6
 
 
@@ -539,7 +540,10 @@ def main():
     traffic = TRACE_DRAM_BYTES_PER_LAUNCH if args.workload in ("cfg2", "band") else None
     probes = ctx.probe_peaks() if not args.no_counters else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_trace",
+                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": ("copied from one ncu capture of k_trace on the 1920x270 band (same wave size)"
+                                   if traffic is not None else None),
+                "kernel": "k_trace",
                 "measured_probes": probes,
                 "frac_of_measured_fp32": (achieved / probes["fp32_tflops"]) if probes else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",

@@ -6,7 +6,7 @@
  * tests, the smoke check and the benchmark's CPU-baseline leg may load it; the
  * CUDA library shares no code with it.
  *
- * Readings taken where the paper is silent (all listed in the design notes):
+ * Readings taken where the paper is silent:
  *  - estimator weight: A = sqrt(beta * L); contribution
  *      (1/(i lambda)) * A * cos(theta) / (r * pdf_A) * exp(i (k r + phi_m))
  *    with pdf_A = pdf_omega * |cos theta_P| / r^2 (area measure at P);
@@ -23,7 +23,7 @@
  *    coherent chain restarts exactly at the hit point (t > 1e-9 m) so that the
  *    optical path length is not perturbed; the hit triangle is excluded.
  *  Parity unpinned: the absolute brightness convention against the paper's
- *  figures and the content of the ambient cache (an input blob here).
+ *  figures (the paper prints no field values).
  */
 #include "oracle.h"
 
@@ -470,6 +470,19 @@ static double cache_lookup(const or_scene *s, v3 p, int ch)
         acc += w * or_half_to_double(s->cache_E[(((size_t)iz * R + iy) * R + ix) * 3 + ch]);
     }
     return acc;
+}
+
+/* the two lookups of a built scene, exposed for the pins */
+double or_tex_lookup(void *h, int32_t tex, double u, double v, int32_t ch)
+{
+    const oracle_t *o = h;
+    return tex_lookup(&o->s, tex, u, v, ch);
+}
+
+double or_cache_lookup(void *h, const double p[3], int32_t ch)
+{
+    const oracle_t *o = h;
+    return cache_lookup(&o->s, mk(p[0], p[1], p[2]), ch);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -105,6 +105,10 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 void or_cone_dir(double lambda, double pitch, double u0, double u1, double d[3], double *pdf);
 int or_closest_hit(void *h, const double o[3], const double d[3], double tmin, double tmax,
                    int brute, double *t, int32_t *tri);
+/* bilinear texture lookup (clamp to edge, texel centres at (i + 1/2) / w) and trilinear
+ * ambient-cache lookup (values at cell centres, [z][y][x][c]) of the scene built into h */
+double or_tex_lookup(void *h, int32_t tex, double u, double v, int32_t ch);
+double or_cache_lookup(void *h, const double p[3], int32_t ch);
 double or_fresnel_dielectric(double cos_i, double n_i, double n_t);
 void or_ggx_eval(double alpha, double F0, const double wo[3], const double wi[3], double *f, double *pdf);
 int or_ggx_sample(double alpha, double F0, const double wo[3], double u0, double u1,

@@ -93,6 +93,10 @@ def _load():
             lib.or_ggx_sample.argtypes = [C.c_double, C.c_double, C.c_void_p, C.c_double, C.c_double,
                                           C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             lib.or_frame.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_tex_lookup.restype = C.c_double
+            lib.or_tex_lookup.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32]
+            lib.or_cache_lookup.restype = C.c_double
+            lib.or_cache_lookup.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
             lib.or_half_to_double.restype = C.c_double
             lib.or_half_to_double.argtypes = [C.c_uint16]
             _lib = lib
@@ -227,6 +231,15 @@ class Oracle:
         d = dict(zip(REC_FIELDS, rec.tolist()))
         d["ok"] = bool(ok)
         return d
+
+    def tex_lookup(self, tex, u, v, ch):
+        """The scene's bilinear texture lookup at (u, v), channel ch."""
+        return self._lib.or_tex_lookup(self._h, int(tex), float(u), float(v), int(ch))
+
+    def cache_lookup(self, p, ch):
+        """The scene's trilinear ambient-cache lookup at world point p, channel ch."""
+        p = np.ascontiguousarray(p, np.float64)
+        return self._lib.or_cache_lookup(self._h, p.ctypes.data, int(ch))
 
     def closest_hit(self, o, d, tmin=0.0, tmax=np.inf, brute=False):
         o = np.ascontiguousarray(o, np.float64)
