@@ -11,7 +11,8 @@ namespace hpt {
     cudaError_t wave_shade_##n(bool, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, int, int, \
                                cudaStream_t);                                                                    \
     cudaError_t wave_accum_##n(const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t); \
-    int wave_occupancy_##n(int);
+    int wave_occupancy_##n(int);                                                                                 \
+    cudaError_t wave_preload_##n();
 HPT_DECL(f64)
 HPT_DECL(df)
 #undef HPT_DECL
@@ -37,4 +38,5 @@ cudaError_t wave_accum(int prec, const JobTable *jt, const WaveDesc &wd, const P
     return prec == 0 ? wave_accum_f64(jt, wd, pb, scr, s) : wave_accum_df(jt, wd, pb, scr, s);
 }
 int wave_occupancy(int prec, int which) { return prec == 0 ? wave_occupancy_f64(which) : wave_occupancy_df(which); }
+cudaError_t wave_preload(int prec) { return prec == 0 ? wave_preload_f64() : wave_preload_df(); }
 }  // namespace hpt

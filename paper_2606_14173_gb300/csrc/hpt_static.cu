@@ -20,21 +20,23 @@ cudaError_t wave_shade(int prec, bool stats, const JobTable *, const WaveDesc &,
 cudaError_t wave_accum(int prec, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t);
 hpt_status internal_make_job(hpt_ctx *, uint64_t, const hpt_render_desc *, void *, size_t, DevJob &);
 int internal_ctx_device(const hpt_ctx *);
-int internal_grid(const hpt_ctx *, int prec, int which);
+void internal_grids(hpt_ctx *, int prec, int &grid_trace, int &grid_shade);
 hpt_status internal_fail(hpt_status st, const char *msg);
+hpt_status internal_check(hpt_ctx *ctx);
 }  // namespace hpt
 
 using namespace hpt;
 
-// The fixed scratch: HPT_FIXED_SCRATCH_BYTES (64 MiB) on every device that loads the library,
-// held until the process exits.  Host code must not use this name as a device address.
+// The fixed scratch: HPT_FIXED_SCRATCH_BYTES (64 MiB) on every device where this module is loaded
+// (hpt_create loads it on the context's device), held until the process exits.  Host code must not
+// use this name as a device address: it takes the address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_fixed_scratch[HPT_FIXED_SCRATCH_BYTES];
 
 namespace {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;                          // serialises the host side of all calls
 void *g_base[MAX_DEVICES] = {nullptr};    // device address of g_fixed_scratch, per device
-JobTable g_host_table;                    // host staging of the one-job table (pageable)
+cudaError_t g_setup_err[MAX_DEVICES] = {};  // why the set-up of a device failed (cudaSuccess: not tried or done)
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t PATH_BYTES = 7 * 8 + 3 * 4 + 4 + 6 * 4 + 3 * 16 + 16 + 4 + 3 * 4 + 3 * 4 + 6 * 4;
@@ -88,6 +90,52 @@ Layout carve(void *base)
 
 static_assert(FIXED_CAPACITY >= 4096, "fixed scratch too small");
 
+// The one-job table of a call, written on the device from a kernel parameter: the launch copies
+// the parameter by value, so no host staging buffer is read after the call returns.
+__global__ void k_put_job(JobTable *t, const DevJob job)
+{
+    t->n_jobs = 1;
+    t->pad = 0;
+    t->jobs[0] = job;
+}
+
+namespace hpt {
+// Set-up of the fixed scratch on 'dev', called by hpt_create with that device current: looks up
+// the array's device address (which loads this module and so places the array in device memory)
+// and clears the status word once.  A failure is recorded and reported by the entry point only.
+void fixed_scratch_setup(int dev)
+{
+    if (dev < 0 || dev >= MAX_DEVICES) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_base[dev]) return;
+    void *ptr = nullptr;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_fixed_scratch);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_put_job);   // loaded now, not at a first call
+    if (e == cudaSuccess) e = cudaMemset(&carve(ptr).scr->status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        g_setup_err[dev] = e;
+        cudaGetLastError();
+        return;
+    }
+    g_base[dev] = ptr;
+}
+
+// The status bits the entry point's kernels left on 'dev' since the last read (then cleared);
+// 0 when the array was never set up there.  Called by hpt_sync after the device synchronised.
+cudaError_t fixed_scratch_status(int dev, unsigned *bits)
+{
+    *bits = 0;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_base[dev]) return cudaSuccess;
+    SlotScratch *scr = carve(g_base[dev]).scr;
+    cudaError_t e = cudaMemcpy(bits, &scr->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && *bits) e = cudaMemset(&scr->status, 0, sizeof(unsigned));
+    return e;
+}
+}  // namespace hpt
+
 #define FS_TRY(call)                                                                              \
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
@@ -101,9 +149,11 @@ static_assert(FIXED_CAPACITY >= 4096, "fixed scratch too small");
 extern "C" hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                                               void *out_dev, size_t out_bytes, void *cuda_stream)
 {
+    hpt_status st = internal_check(ctx);   // clears the thread's last error, sets the device
+    if (st) return st;
     if (!out_dev) return internal_fail(HPT_ERR_INVALID_ARG, "out_dev is NULL");
     DevJob J;
-    hpt_status st = internal_make_job(ctx, scene_id, desc, out_dev, out_bytes, J);   // sets the device
+    st = internal_make_job(ctx, scene_id, desc, out_dev, out_bytes, J);
     if (st) return st;
     if (J.spp > FIXED_CAPACITY) {
         char m[160];
@@ -112,22 +162,22 @@ extern "C" hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, c
     }
     const int dev = internal_ctx_device(ctx);
     if (dev < 0 || dev >= MAX_DEVICES) return internal_fail(HPT_ERR_UNSUPPORTED, "device index out of range");
+    int grid_trace = 1, grid_shade = 1;
+    const int prec = desc->precision;
+    internal_grids(ctx, prec, grid_trace, grid_shade);
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_base[dev]) {
-        // set-up, once per device, with that device current: the array's device address
-        void *ptr = nullptr;
-        FS_TRY(cudaGetSymbolAddress(&ptr, g_fixed_scratch));
-        g_base[dev] = ptr;
+        char m[200];
+        snprintf(m, sizeof m, "the fixed scratch array is not available on device %d: %s", dev,
+                 g_setup_err[dev] != cudaSuccess ? cudaGetErrorString(g_setup_err[dev]) : "not set up");
+        return internal_fail(HPT_ERR_UNSUPPORTED, m);
     }
     const Layout L = carve(g_base[dev]);
-    const int prec = desc->precision;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    g_host_table.n_jobs = 1;
-    g_host_table.jobs[0] = J;
-    FS_TRY(cudaMemcpyAsync(L.table, &g_host_table, offsetof(JobTable, jobs) + sizeof(DevJob), cudaMemcpyHostToDevice, s));
-    // the array keeps the previous call's contents: clear the status word now, the queue
-    // counters before every wave
-    FS_TRY(cudaMemsetAsync(&L.scr->status, 0, sizeof(unsigned), s));
+    k_put_job<<<1, 1, 0, s>>>(L.table, J);
+    FS_TRY(cudaGetLastError());
+    // the array keeps the previous call's contents: the queue counters are cleared before every
+    // wave; the status word is sticky until hpt_sync reads it
     const int n_iter = J.max_depth + 1;
     long long c = 0;
     while (c < J.n_items) {
@@ -145,8 +195,8 @@ extern "C" hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, c
         FS_TRY(cudaMemsetAsync(L.scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), s));
         FS_TRY(wave_gen(prec, L.table, wd, L.pb, L.scr, s));
         for (int it = 0; it < n_iter; ++it) {
-            FS_TRY(wave_trace(prec, false, L.table, wd, L.pb, L.scr, it, internal_grid(ctx, prec, 0), s));
-            FS_TRY(wave_shade(prec, false, L.table, wd, L.pb, L.scr, it, internal_grid(ctx, prec, 1), s));
+            FS_TRY(wave_trace(prec, false, L.table, wd, L.pb, L.scr, it, grid_trace, s));
+            FS_TRY(wave_shade(prec, false, L.table, wd, L.pb, L.scr, it, grid_shade, s));
         }
         FS_TRY(wave_accum(prec, L.table, wd, L.pb, L.scr, s));
         c += take;

@@ -21,4 +21,5 @@ cudaError_t wave_accum_df(const JobTable *jt, const WaveDesc &wd, const PathBufs
     return WaveLaunch<df>::accum(jt, wd, pb, scr, s);
 }
 int wave_occupancy_df(int which) { return WaveLaunch<df>::occupancy(which); }
+cudaError_t wave_preload_df() { return WaveLaunch<df>::preload(); }
 }  // namespace hpt

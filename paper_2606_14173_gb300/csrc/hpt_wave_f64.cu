@@ -21,4 +21,5 @@ cudaError_t wave_accum_f64(const JobTable *jt, const WaveDesc &wd, const PathBuf
     return WaveLaunch<double>::accum(jt, wd, pb, scr, s);
 }
 int wave_occupancy_f64(int which) { return WaveLaunch<double>::occupancy(which); }
+cudaError_t wave_preload_f64() { return WaveLaunch<double>::preload(); }
 }  // namespace hpt

@@ -38,6 +38,21 @@ template <class R> struct WaveLaunch {
         if (g > 0) k_accum<R><<<g, ACCUM_BLOCK, 0, s>>>(jt, wd, pb, scr);
         return cudaGetLastError();
     }
+    // load every kernel of this arithmetic now (with lazy module loading a kernel is otherwise
+    // loaded, and its code placed in device memory, at its first launch)
+    static cudaError_t preload()
+    {
+        cudaFuncAttributes a;
+        cudaError_t e = cudaFuncGetAttributes(&a, k_gen<R>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_trace<R, false>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_trace<R, true>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_shade<R, false, true>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_shade<R, false, false>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_shade<R, true, true>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_shade<R, true, false>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_accum<R>);
+        return e;
+    }
     // resident blocks per SM of the trace (0) and shade (1) kernels; the trace kernel asks for
     // no more shared memory than its traversal stacks need, leaving the rest of the SM's on-chip
     // memory to the L1 cache that holds the BVH
