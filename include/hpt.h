@@ -50,7 +50,8 @@ enum {
     HPT_ERR_BUSY = -5,          /* serving queue full / admission refused                 */
     HPT_ERR_NOT_FOUND = -6,     /* unknown scene or request id                            */
     HPT_ERR_UNSUPPORTED = -7,   /* valid request outside what this build supports         */
-    HPT_ERR_DEVICE = -8         /* the kernel reported an internal error (status word)    */
+    HPT_ERR_DEVICE = -8,        /* the kernel reported an internal error (status word)    */
+    HPT_ERR_CANCELLED = -9      /* the request was cancelled (hpt_cancel)                 */
 };
 
 /* material kinds (Sec. 4.2: mirror and dielectric are delta lobes, the rest non-delta) */
@@ -63,7 +64,11 @@ enum { HPT_PREC_FP64 = 0, HPT_PREC_DF32 = 1 };
 typedef struct hpt_ctx hpt_ctx;
 
 /* context flags */
-enum { HPT_CTX_NO_GRAPHS = 1 };   /* hpt_trace launches every kernel instead of replaying frames */
+enum {
+    HPT_CTX_NO_GRAPHS = 1,          /* hpt_trace launches every kernel instead of replaying frames   */
+    HPT_CTX_FAIL_SERVING_WAVES = 2  /* for tests of the failure path: every serving wave fails to be
+                                       issued as if its wave state could not be allocated (OOM)     */
+};
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* serving admission limit for in-flight outputs; 0 = 60 % of
@@ -309,18 +314,42 @@ hpt_status hpt_scene_set_cache(hpt_ctx *ctx, uint64_t scene_id, int32_t res, con
 
 /* ---- serving: continuous batching of render requests ---------------------------------- */
 /* Queue a request; the scheduler thread admits it when a slot and memory are free and runs
- * it concurrently with the requests already on the device.  out_dev is caller-owned and must
- * stay valid until the request completes.  HPT_ERR_BUSY (nothing queued) when max_queue
- * requests already wait for admission. */
+ * it concurrently with the requests already on the device (the waves of all admitted requests
+ * share the device; a request's fields equal those of the same render traced alone).
+ *  out_dev != NULL: caller-owned device output (complex64 [n_lambda][K][H][W], out_bytes >= its
+ *    size); it must stay valid until the request is done.  Admission counts its bytes against the
+ *    context's hbm_budget_bytes.
+ *  out_dev == NULL: the library allocates the output when it admits the request, and only while
+ *    the device's free memory (cudaMemGetInfo at admission, so scenes, caches and every other
+ *    allocation on the device are accounted for) minus a reserve of max(1 GiB, 5 % of the device)
+ *    holds it; the request waits in the queue until then.  A request that does not fit even with
+ *    nothing else admitted finishes with HPT_ERR_OOM.  Read the result with hpt_request_output and
+ *    free it with hpt_request_release.
+ * HPT_ERR_BUSY (nothing queued) when max_queue requests already wait for admission. */
 hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                       void *out_dev, size_t out_bytes, uint64_t *req_id);
-/* *done = 1 when the request finished (its output is complete). */
+/* *done = 1 when the request finished; then returns its final status (HPT_OK, or the error that
+ * ended it, e.g. HPT_ERR_DEVICE with the kernels' status bits, HPT_ERR_OOM, HPT_ERR_CUDA or
+ * HPT_ERR_CANCELLED, with the message in hpt_last_error()); HPT_OK while it runs. */
 hpt_status hpt_poll(hpt_ctx *ctx, uint64_t req_id, int *done);
-/* Wait up to timeout_ms (0 = forever) for the request; HPT_ERR_TIMEOUT if not done. */
+/* Wait up to timeout_ms (0 = forever) for the request; HPT_ERR_TIMEOUT if not done, else its
+ * final status as hpt_poll reports it.  A request is done only when no kernel of it is still
+ * running: its output (complete when the status is HPT_OK) may then be read or freed. */
 hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_ms);
+/* Cancel a request: a queued one is dropped at once, an admitted one gets no further waves and
+ * is done when its waves in flight have completed; its final status is HPT_ERR_CANCELLED.  A
+ * finished request is left as it is (HPT_OK). */
+hpt_status hpt_cancel(hpt_ctx *ctx, uint64_t req_id);
 /* Timestamps of a finished request in microseconds since the context was created:
- * t[0] submitted, t[1] admitted (launched), t[2] completed. */
+ * t[0] submitted, t[1] admitted (launched; -1 if never admitted), t[2] completed. */
 hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[3]);
+/* Copy the library-owned output of a finished request (submitted with out_dev == NULL) to dst
+ * (host or device memory, bytes >= its size); synchronous. */
+hpt_status hpt_request_output(hpt_ctx *ctx, uint64_t req_id, void *dst, size_t bytes);
+/* Forget a finished request and free its library-owned output; its id becomes unknown.  Records
+ * of finished requests are otherwise kept until 4096 newer requests have finished, then dropped
+ * oldest first (with their library-owned outputs). */
+hpt_status hpt_request_release(hpt_ctx *ctx, uint64_t req_id);
 
 /* ---- trace with fixed scratch: an entry point that allocates nothing -------------------
  * The paper has no counterpart; this is an interface for callers that cannot allocate device
@@ -333,19 +362,22 @@ hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[3]);
  * layout, bitwise the same fields) but takes every scratch buffer of the trace -- the path
  * state of a wave, the ray queues and their counters, the device copy of the render job --
  * from one device array of HPT_FIXED_SCRATCH_BYTES (64 MiB) that the library defines at file
- * scope; every GPU that loads the library holds that array until the process exits.  The call
- * issues no cudaMalloc, cudaFree or other allocating routine.  The context, the uploaded
- * scene (device memory allocated earlier by hpt_create / hpt_scene_upload) and out_dev
- * (caller-owned, complex64 [n_lambda][K][H][W], out_bytes >= 8 n_lambda K H W) are its inputs
- * and output.  The work is queued asynchronously on cuda_stream.
- *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- *    with that device current); make that first call before any stream capture.
+ * scope.  The call issues no cudaMalloc, cudaFree or other allocating routine.  The context,
+ * the uploaded scene (device memory allocated earlier by hpt_create / hpt_scene_upload) and
+ * out_dev (caller-owned, complex64 [n_lambda][K][H][W], out_bytes >= 8 n_lambda K H W) are its
+ * inputs and output.  The work is queued asynchronously on cuda_stream.
+ *  - Set-up: hpt_create, with its device current, looks up the array's device address
+ *    (cudaGetSymbolAddress), which places the array in that device's memory; the array then
+ *    stays there until the process exits.  The entry point itself does no set-up; if the
+ *    set-up failed on the context's device it returns HPT_ERR_UNSUPPORTED with the cause.
  *  - Frames of any size are split into waves that fit the array; spp larger than the array's
  *    path capacity (about 300k paths) is rejected with HPT_ERR_INVALID_ARG.
- *  - All calls share the one array and it keeps the last call's contents; the call clears what
- *    must start at zero.  Calls whose work overlaps on the GPU (on different streams, or from
- *    different contexts on one device) race on the array: serialise them on one stream.
- *  - Device-side status bits of this entry point are not reported by hpt_sync.            */
+ *  - All calls share the one array and it keeps the last call's contents; each call clears
+ *    what must start at zero (the queue counters of every wave).  Calls whose work overlaps on
+ *    the GPU (on different streams, or from different contexts on one device) race on the
+ *    array: serialise them on one stream.
+ *  - The kernels' status bits (e.g. a traversal-stack overflow) accumulate in the array and
+ *    are reported, then cleared, by the next hpt_sync on a context of that device.          */
 #define HPT_FIXED_SCRATCH_BYTES (64u << 20)
 hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                                    void *out_dev, size_t out_bytes, void *cuda_stream);

@@ -20,6 +20,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hpt.h"
 #include "hpt_internal.h"
@@ -32,6 +33,9 @@ cudaError_t wave_shade(int prec, bool stats, const JobTable *, const WaveDesc &,
                        int grid, cudaStream_t);
 cudaError_t wave_accum(int prec, const JobTable *, const WaveDesc &, const PathBufs &, SlotScratch *, cudaStream_t);
 int wave_occupancy(int prec, int which);
+cudaError_t wave_preload(int prec);
+void fixed_scratch_setup(int dev);
+cudaError_t fixed_scratch_status(int dev, unsigned *bits);
 }  // namespace hpt
 
 using namespace hpt;
@@ -236,13 +240,22 @@ struct Request {
     int prec = 1;
     long long next = 0;          // next work item to schedule
     size_t out_bytes = 0;
+    bool lib_out = false;        // the output is allocated by the library at admission
+    void *out_lib = nullptr;     // that output (device), until hpt_request_release
     double t_submit = 0, t_admit = -1, t_done = -1;
+    bool admitted = false;
+    bool stopped = false;        // no more waves: cancelled or a wave failed to issue
+    int waves = 0;               // issued waves carrying its items that have not completed
+    unsigned dev_bits = 0;       // kernel status bits of those waves
+    hpt_status status = HPT_OK;  // final status once done
+    std::string err;             // message of a failed status
     bool done = false;
 };
 
 struct InflightWave {
     cudaEvent_t ev = nullptr;
-    std::vector<std::shared_ptr<Request>> finishing;   // requests whose last items are in this wave
+    int status_slot = -1;                               // pinned word holding the wave's status bits
+    std::vector<std::shared_ptr<Request>> carried;      // requests with items in this wave
 };
 
 struct hpt_ctx {
@@ -315,13 +328,19 @@ struct hpt_ctx {
     uint64_t budget = 0;                 // device bytes of in-flight request outputs
     int max_inflight = 8;                // requests on the device at once
     size_t max_queue = 4096;             // pending requests before hpt_submit says BUSY
+    int flags = 0;                       // HPT_CTX_* of the descriptor
     std::mutex smu;
     std::condition_variable scv, dcv;
     std::deque<std::shared_ptr<Request>> pending;
     std::vector<std::shared_ptr<Request>> active;
     std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    std::deque<uint64_t> finished;       // ids of finished requests, oldest first (bounded retention)
     std::deque<InflightWave> inflight;
     std::vector<cudaEvent_t> free_events;
+    static constexpr int STATUS_SLOTS = 16;
+    unsigned *h_wave_status = nullptr;   // pinned, one word per in-flight serving wave
+    bool status_slot_used[STATUS_SLOTS] = {};
+    cudaStream_t ostream = nullptr;      // allocation, copy-out and release of library-owned outputs
     uint64_t next_req = 1;
     uint64_t bytes_active = 0;           // outputs of admitted, not yet finished requests
     int live = 0;                        // admitted, not yet finished requests
@@ -360,11 +379,13 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     ctx->t0 = std::chrono::steady_clock::now();
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
     for (int prec = 0; prec < 2; ++prec) {
+        CUDA_TRY(wave_preload(prec));   // all wave kernels loaded now, not at a first launch
         ctx->grid_trace[prec] = ctx->sm_count * wave_occupancy(prec, 0);
         ctx->grid_shade[prec] = ctx->sm_count * wave_occupancy(prec, 1);
     }
     if (const char *e = getenv("HPT_WAVE_PATHS")) ctx->capacity = std::max(1 << 12, std::min(atoi(e), 1 << 26));
     if (const char *e = getenv("HPT_DEBUG_WAVES")) ctx->debug_waves = atoi(e);
+    if (desc) ctx->flags = desc->flags;
     if (desc && (desc->flags & HPT_CTX_NO_GRAPHS)) ctx->use_graphs = false;
     if (const char *e = getenv("HPT_GRAPHS")) ctx->use_graphs = atoi(e) != 0;
     CUDA_TRY(cudaMalloc(&ctx->d_scr, sizeof(SlotScratch)));
@@ -377,6 +398,8 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
         CUDA_TRY(cudaMalloc(&ctx->d_scr_x[l], sizeof(SlotScratch)));
         CUDA_TRY(cudaMemset(ctx->d_scr_x[l], 0, sizeof(SlotScratch)));
     }
+    CUDA_TRY(cudaMallocHost(&ctx->h_wave_status, sizeof(unsigned) * hpt_ctx::STATUS_SLOTS));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->ostream, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     // cos/sin(2 pi k / 256) split into float pairs for the double-float cone sampler
@@ -405,6 +428,8 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
         CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         ctx->budget = (uint64_t)(fr * 0.6);
     }
+    // the fixed-scratch entry point's array on this device (see hpt_trace_fixed_scratch)
+    fixed_scratch_setup(device);
     hpt_ctx *raw = ctx.release();
     raw->sched = std::thread(sched_loop, raw);
     *out = raw;
@@ -424,7 +449,12 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->sched.joinable()) ctx->sched.join();
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (auto &w : ctx->inflight) cudaEventDestroy(w.ev);
+    for (auto &w : ctx->inflight)
+        if (w.ev) cudaEventDestroy(w.ev);
+    for (auto &kv : ctx->reqs)
+        if (kv.second->out_lib) cudaFree(kv.second->out_lib);
+    if (ctx->h_wave_status) cudaFreeHost(ctx->h_wave_status);
+    if (ctx->ostream) cudaStreamDestroy(ctx->ostream);
     for (auto &g : ctx->graphs) free_frame(g);
     for (auto e : ctx->free_events) cudaEventDestroy(e);
     for (auto &kv : ctx->scenes) {
@@ -1173,8 +1203,11 @@ extern "C" hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_rende
     st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (ctx->use_graphs && ctx->debug_waves == 0) return run_graph(ctx, J, desc->precision, (cudaStream_t)stream);
-    return run_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream);
+    nvtxRangePushA("hpt_trace frame");
+    st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, (cudaStream_t)stream)
+                                                  : run_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream);
+    nvtxRangePop();
+    return st;
 }
 
 extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out_host,
@@ -1200,6 +1233,10 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
     }
     J.out = (float2 *)ctx->host_out_dev;
     cudaStream_t s = (cudaStream_t)stream;
+    struct Range {
+        Range() { nvtxRangePushA("hpt_trace_host frame + copy"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     // the device staging buffer is the context's, so the frame's captured graph is reused
     st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, s)
                                                   : run_jobs(ctx, &J, 1, desc->precision, false, s);
@@ -1218,11 +1255,9 @@ static hpt_status read_status(hpt_ctx *ctx)
         CUDA_TRY(cudaMemcpy(&b2, &ctx->d_scr_x[l]->status, sizeof b2, cudaMemcpyDeviceToHost));
         bits |= b2;
     }
-    for (int l = 0; l < HPT_LANES; ++l) {
-        if (!ctx->sscr[l]) continue;
+    {
         unsigned b2 = 0;
-        CUDA_TRY(cudaMemcpy(&b2, &ctx->sscr[l]->status, sizeof b2, cudaMemcpyDeviceToHost));
-        if (b2) CUDA_TRY(cudaMemset(&ctx->sscr[l]->status, 0, sizeof b2));
+        CUDA_TRY(fixed_scratch_status(ctx->device, &b2));
         bits |= b2;
     }
     if (bits) {
@@ -1508,13 +1543,47 @@ extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_re
 
 // ------------------------------------------------------------------------------ serving
 // Continuous batching.  A scheduler thread admits queued requests while fewer than
-// max_inflight are active and their outputs fit the HBM budget, then keeps the device busy
-// with waves: each wave takes an equal share of its paths from every active request of one
-// arithmetic (round robin), so requests that arrive while others are running join the next
-// wave and their work overlaps on the device.  Two waves are queued ahead; a request is
-// complete when the wave that carries its last items finishes.  Per-pixel results do not
-// depend on how items are grouped into waves, so a request's fields are the same alone and in
-// the mix.
+// max_inflight are active and their outputs fit in memory (caller-owned outputs: the HBM budget;
+// library-owned outputs: allocated at admission, only while the device's free memory minus a
+// reserve holds them), then keeps the device busy with waves: each wave takes an equal share of
+// its paths from every active request of one arithmetic (round robin), so requests that arrive
+// while others are running join the next wave and their work overlaps on the device.  A wave
+// records its lane's kernel status bits into a pinned word of its own; a request is complete
+// when the last wave carrying its items has completed, with the status bits of all of them.
+// Per-pixel results do not depend on how items are grouped into waves, so a request's fields are
+// the same alone and in the mix.
+constexpr size_t FINISHED_KEPT = 4096;     // finished requests kept queryable (oldest dropped)
+
+static size_t out_reserve_bytes(size_t total) { return std::max<size_t>(size_t(1) << 30, total / 20); }
+
+// a request leaves the device's books; caller holds smu
+static void finish_request(hpt_ctx *ctx, const std::shared_ptr<Request> &r, double now)
+{
+    r->done = true;
+    r->t_done = now;
+    if (r->status == HPT_OK && r->dev_bits) {
+        char m[160];
+        snprintf(m, sizeof m, "request %llu: kernel status 0x%x%s%s%s", (unsigned long long)r->id, r->dev_bits,
+                 (r->dev_bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
+                 (r->dev_bits & ST_BAD_JOB) ? " bad-job" : "", (r->dev_bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
+        r->status = HPT_ERR_DEVICE;
+        r->err = m;
+    }
+    if (r->admitted) {
+        ctx->bytes_active -= r->out_bytes;
+        ctx->live--;
+    }
+    r->scene->users--;
+    ctx->finished.push_back(r->id);
+    while (ctx->finished.size() > FINISHED_KEPT) {
+        auto it = ctx->reqs.find(ctx->finished.front());
+        ctx->finished.pop_front();
+        if (it == ctx->reqs.end()) continue;
+        if (it->second->out_lib) cudaFreeAsync(it->second->out_lib, ctx->ostream);
+        ctx->reqs.erase(it);
+    }
+}
+
 static void retire_oldest(hpt_ctx *ctx)
 {
     InflightWave w;
@@ -1529,16 +1598,82 @@ static void retire_oldest(hpt_ctx *ctx)
         std::lock_guard<std::mutex> lk(ctx->smu);
         ctx->inflight.pop_front();
         ctx->free_events.push_back(w.ev);
-        for (auto &r : w.finishing) {
-            r->done = true;
-            r->t_done = now;
-            ctx->bytes_active -= r->out_bytes;
-            ctx->live--;
-            r->scene->users--;
+        const unsigned bits = ctx->h_wave_status[w.status_slot];
+        ctx->status_slot_used[w.status_slot] = false;
+        for (auto &r : w.carried) {
+            r->dev_bits |= bits;
+            if (--r->waves == 0 && (r->stopped || r->next >= r->job.n_items)) finish_request(ctx, r, now);
         }
     }
     ctx->dcv.notify_all();
     ctx->scv.notify_all();
+}
+
+// the requests of a wave that could not be issued stop here; caller holds smu
+static void stop_requests(hpt_ctx *ctx, const std::vector<std::pair<std::shared_ptr<Request>, int>> &picks, hpt_status st,
+                          const std::string &msg)
+{
+    const double now = ctx->now_us();
+    for (auto &pk : picks) {
+        auto &r = pk.first;
+        if (r->stopped) continue;
+        r->stopped = true;
+        r->status = st;
+        r->err = msg;
+        auto it = std::find(ctx->active.begin(), ctx->active.end(), r);
+        if (it != ctx->active.end()) ctx->active.erase(it);
+        if (r->waves == 0) finish_request(ctx, r, now);
+    }
+}
+
+// admission of the oldest pending request; caller holds smu
+static bool try_admit(hpt_ctx *ctx)
+{
+    if (ctx->pending.empty() || ctx->live >= ctx->max_inflight) return false;
+    auto r = ctx->pending.front();
+    if (ctx->live > 0 && ctx->bytes_active + r->out_bytes > ctx->budget) return false;
+    if (r->lib_out) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
+        const size_t reserve = out_reserve_bytes(tot);
+        if (fr < reserve || fr - reserve < r->out_bytes) {
+            // nothing else on the device will free memory for it: refuse it rather than wait
+            if (ctx->live > 0) return false;
+            ctx->pending.pop_front();
+            r->status = HPT_ERR_OOM;
+            r->err = "request output does not fit in the device's free memory";
+            r->stopped = true;
+            finish_request(ctx, r, ctx->now_us());
+            return true;
+        }
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, r->out_bytes, ctx->ostream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->ostream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (p) cudaFreeAsync(p, ctx->ostream);
+            if (ctx->live > 0) return false;
+            ctx->pending.pop_front();
+            r->status = HPT_ERR_OOM;
+            r->err = std::string("request output: ") + cudaGetErrorString(e);
+            r->stopped = true;
+            finish_request(ctx, r, ctx->now_us());
+            return true;
+        }
+        r->out_lib = p;
+        r->job.out = (float2 *)p;
+    }
+    ctx->pending.pop_front();
+    r->t_admit = ctx->now_us();
+    r->admitted = true;
+    ctx->bytes_active += r->out_bytes;
+    ctx->live++;
+    if (r->job.n_items == 0) {
+        finish_request(ctx, r, r->t_admit);
+        return true;
+    }
+    ctx->active.push_back(r);
+    return true;
 }
 
 static void sched_loop(hpt_ctx *ctx)
@@ -1548,6 +1683,7 @@ static void sched_loop(hpt_ctx *ctx)
         std::vector<std::pair<std::shared_ptr<Request>, int>> picks;
         int prec = -1;
         bool idle_wait = false;
+        int slot_idx = -1;
         {
             std::unique_lock<std::mutex> lk(ctx->smu);
             auto schedulable = [&] {
@@ -1563,16 +1699,9 @@ static void sched_loop(hpt_ctx *ctx)
                 idle_wait = true;   // drain what is in flight, start nothing new
                 goto unlocked;
             }
-            // admission: slots and HBM budget
-            while (!ctx->stop && !ctx->pending.empty() && ctx->live < ctx->max_inflight &&
-                   (ctx->live == 0 || ctx->bytes_active + ctx->pending.front()->out_bytes <= ctx->budget)) {
-                auto r = ctx->pending.front();
-                ctx->pending.pop_front();
-                r->t_admit = ctx->now_us();
-                ctx->bytes_active += r->out_bytes;
-                ctx->live++;
-                ctx->active.push_back(r);
-            }
+            bool admitted_any = false;
+            while (!ctx->stop && try_admit(ctx)) admitted_any = true;
+            if (admitted_any) ctx->dcv.notify_all();
             // one wave: equal path shares of the active requests that use one arithmetic
             std::vector<std::shared_ptr<Request>> cand;
             const size_t na = ctx->active.size();
@@ -1583,6 +1712,11 @@ static void sched_loop(hpt_ctx *ctx)
                 if (r->prec == prec && (int)cand.size() < MAX_SEG) cand.push_back(r);
             }
             if (!cand.empty()) {
+                for (int k = 0; k < hpt_ctx::STATUS_SLOTS; ++k)
+                    if (!ctx->status_slot_used[k]) { slot_idx = k; break; }
+            }
+            if (!cand.empty() && slot_idx >= 0) {
+                ctx->status_slot_used[slot_idx] = true;
                 ctx->rr = (ctx->rr + 1) % std::max<size_t>(na, 1);
                 const long long share = std::max<long long>(1, (long long)ctx->capacity / (long long)cand.size());
                 for (auto &r : cand) {
@@ -1597,10 +1731,14 @@ static void sched_loop(hpt_ctx *ctx)
     unlocked:
         if (!picks.empty()) {
             hpt_status st = HPT_OK;
+            std::string msg;
             InflightWave w;
+            w.status_slot = slot_idx;
             {
                 std::lock_guard<std::mutex> lk(ctx->mu);
-                st = ensure_sched_paths(ctx);
+                nvtxRangePushA("hpt serving wave");
+                if (ctx->flags & HPT_CTX_FAIL_SERVING_WAVES) st = fail(HPT_ERR_OOM, "serving wave state: injected failure");
+                if (!st) st = ensure_sched_paths(ctx);
                 Slot *slot = st ? nullptr : acquire_slot(ctx);
                 WaveDesc wd;
                 memset(&wd, 0, sizeof wd);
@@ -1628,16 +1766,21 @@ static void sched_loop(hpt_ctx *ctx)
                     const PathBufs &lpb = ctx->spb[lane];
                     SlotScratch *lscr = ctx->sscr[lane];
                     const int n_iter = max_depth + 1;
-                    bool ok = cudaMemcpyAsync(slot->d_table, h, offsetof(JobTable, jobs) + sizeof(DevJob) * h->n_jobs,
-                                              cudaMemcpyHostToDevice, ws) == cudaSuccess;
-                    ok = ok && cudaMemsetAsync(lscr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws) == cudaSuccess;
-                    ok = ok && wave_gen(prec, slot->d_table, wd, lpb, lscr, ws) == cudaSuccess;
-                    for (int it = 0; ok && it < n_iter; ++it) {
-                        ok = wave_trace(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_trace[prec], ws) == cudaSuccess;
-                        ok = ok && wave_shade(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_shade[prec], ws) == cudaSuccess;
+                    cudaError_t e = cudaMemcpyAsync(slot->d_table, h, offsetof(JobTable, jobs) + sizeof(DevJob) * h->n_jobs,
+                                                    cudaMemcpyHostToDevice, ws);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(lscr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), ws);
+                    if (e == cudaSuccess) e = wave_gen(prec, slot->d_table, wd, lpb, lscr, ws);
+                    for (int it = 0; e == cudaSuccess && it < n_iter; ++it) {
+                        e = wave_trace(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_trace[prec], ws);
+                        if (e == cudaSuccess) e = wave_shade(prec, false, slot->d_table, wd, lpb, lscr, it, ctx->grid_shade[prec], ws);
                     }
-                    ok = ok && wave_accum(prec, slot->d_table, wd, lpb, lscr, ws) == cudaSuccess;
-                    ok = ok && cudaEventRecord(slot->done, ws) == cudaSuccess;
+                    if (e == cudaSuccess) e = wave_accum(prec, slot->d_table, wd, lpb, lscr, ws);
+                    if (e == cudaSuccess) e = cudaEventRecord(slot->done, ws);
+                    // the wave's status bits: copied to its own pinned word, then cleared on the lane
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(ctx->h_wave_status + slot_idx, &lscr->status, sizeof(unsigned),
+                                            cudaMemcpyDeviceToHost, ws);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(&lscr->status, 0, sizeof(unsigned), ws);
                     {
                         std::lock_guard<std::mutex> lk2(ctx->smu);
                         if (!ctx->free_events.empty()) {
@@ -1645,30 +1788,43 @@ static void sched_loop(hpt_ctx *ctx)
                             ctx->free_events.pop_back();
                         }
                     }
-                    if (!w.ev) cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
-                    // the wave's event also covers the waves issued before it on the other lanes,
-                    // so that a request counts as done only when all its waves are (the waits
-                    // follow this wave's kernels and hold back nothing but the event)
-                    for (int l = 0; ok && l < HPT_LANES; ++l)
-                        if (l != lane) ok = cudaStreamWaitEvent(ws, ctx->slane_ev[l], 0) == cudaSuccess;
-                    ok = ok && cudaEventRecord(w.ev, ws) == cudaSuccess;
-                    ok = ok && cudaEventRecord(ctx->slane_ev[lane], ws) == cudaSuccess;
-                    if (!ok) st = HPT_ERR_CUDA;
+                    if (!w.ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
+                    if (e == cudaSuccess) e = cudaEventRecord(w.ev, ws);
+                    if (e == cudaSuccess) e = cudaEventRecord(ctx->slane_ev[lane], ws);
+                    if (e != cudaSuccess) {
+                        // nothing of a failed wave may still run once its requests are reported
+                        cudaStreamSynchronize(ws);
+                        st = fail(HPT_ERR_CUDA, "serving wave: %s", cudaGetErrorString(e));
+                        cudaGetLastError();
+                    }
                 }
+                if (st) msg = g_err;
+                nvtxRangePop();
             }
             {
                 std::lock_guard<std::mutex> lk(ctx->smu);
-                for (auto &pk : picks) {
-                    Request &r = *pk.first;
-                    r.next += pk.second;
-                    if (r.next >= r.job.n_items) {
-                        w.finishing.push_back(pk.first);
-                        ctx->active.erase(std::find(ctx->active.begin(), ctx->active.end(), pk.first));
+                if (st) {
+                    if (w.ev) ctx->free_events.push_back(w.ev);
+                    ctx->status_slot_used[slot_idx] = false;
+                    stop_requests(ctx, picks, st, msg);
+                } else {
+                    for (auto &pk : picks) {
+                        Request &r = *pk.first;
+                        r.next += pk.second;
+                        r.waves++;
+                        w.carried.push_back(pk.first);
+                        if (r.next >= r.job.n_items) {
+                            auto it = std::find(ctx->active.begin(), ctx->active.end(), pk.first);
+                            if (it != ctx->active.end()) ctx->active.erase(it);
+                        }
                     }
+                    ctx->inflight.push_back(w);
                 }
-                ctx->inflight.push_back(w);
             }
-            (void)st;
+            if (st) {
+                ctx->dcv.notify_all();
+                continue;
+            }
         }
         // keep at most one wave per lane queued ahead; retire finished ones
         size_t nin;
@@ -1687,15 +1843,16 @@ extern "C" hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_rend
     g_err.clear();
     hpt_status st = check_ctx(ctx);
     if (st) return st;
-    if (!out_dev || !req_id) return fail(HPT_ERR_INVALID_ARG, "out_dev or req_id is NULL");
+    if (!req_id) return fail(HPT_ERR_INVALID_ARG, "req_id is NULL");
     auto r = std::make_shared<Request>();
     SceneRec *rec = nullptr;
-    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, r->job, &rec);
+    st = make_job(ctx, scene_id, desc, out_dev, out_dev ? out_bytes : 0, r->job, &rec);
     if (st) return st;
     if (r->job.spp > ctx->capacity) return fail(HPT_ERR_UNSUPPORTED, "spp exceeds the wave capacity");
     r->scene = rec;
     r->prec = desc->precision;
     r->out_bytes = (size_t)8 * desc->n_lambda * desc->K * (size_t)desc->W * desc->H;
+    r->lib_out = out_dev == nullptr;
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
         if (ctx->stop) return fail(HPT_ERR_BUSY, "context is shutting down");
@@ -1717,6 +1874,13 @@ static std::shared_ptr<Request> find_req(hpt_ctx *ctx, uint64_t id)
     return it == ctx->reqs.end() ? nullptr : it->second;
 }
 
+// the final status of a finished request, with its message for this thread
+static hpt_status req_status(const Request &r)
+{
+    if (r.status != HPT_OK) return fail(r.status, "%s", r.err.c_str());
+    return HPT_OK;
+}
+
 extern "C" hpt_status hpt_poll(hpt_ctx *ctx, uint64_t req_id, int *done)
 {
     g_err.clear();
@@ -1725,7 +1889,7 @@ extern "C" hpt_status hpt_poll(hpt_ctx *ctx, uint64_t req_id, int *done)
     auto r = find_req(ctx, req_id);
     if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
     *done = r->done ? 1 : 0;
-    return HPT_OK;
+    return r->done ? req_status(*r) : HPT_OK;
 }
 
 extern "C" hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_ms)
@@ -1738,6 +1902,29 @@ extern "C" hpt_status hpt_wait(hpt_ctx *ctx, uint64_t req_id, uint32_t timeout_m
     if (timeout_ms == 0) ctx->dcv.wait(lk, [&] { return r->done; });
     else if (!ctx->dcv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
         return fail(HPT_ERR_TIMEOUT, "request %llu not done after %u ms", (unsigned long long)req_id, timeout_ms);
+    return req_status(*r);
+}
+
+extern "C" hpt_status hpt_cancel(hpt_ctx *ctx, uint64_t req_id)
+{
+    g_err.clear();
+    if (!ctx) return fail(HPT_ERR_INVALID_ARG, "ctx is NULL");
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        auto r = find_req(ctx, req_id);
+        if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+        if (r->done || r->stopped) return HPT_OK;
+        r->stopped = true;
+        r->status = HPT_ERR_CANCELLED;
+        r->err = "request cancelled";
+        auto pit = std::find(ctx->pending.begin(), ctx->pending.end(), r);
+        if (pit != ctx->pending.end()) ctx->pending.erase(pit);
+        auto ait = std::find(ctx->active.begin(), ctx->active.end(), r);
+        if (ait != ctx->active.end()) ctx->active.erase(ait);
+        if (r->waves == 0) finish_request(ctx, r, ctx->now_us());   // else when its last wave completes
+    }
+    ctx->dcv.notify_all();
+    ctx->scv.notify_all();
     return HPT_OK;
 }
 
@@ -1754,6 +1941,47 @@ extern "C" hpt_status hpt_request_times(hpt_ctx *ctx, uint64_t req_id, double t[
     return r->done ? HPT_OK : fail(HPT_ERR_BUSY, "request %llu not done", (unsigned long long)req_id);
 }
 
+extern "C" hpt_status hpt_request_output(hpt_ctx *ctx, uint64_t req_id, void *dst, size_t bytes)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!dst) return fail(HPT_ERR_INVALID_ARG, "dst is NULL");
+    void *src = nullptr;
+    size_t n = 0;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        auto r = find_req(ctx, req_id);
+        if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+        if (!r->done) return fail(HPT_ERR_BUSY, "request %llu not done", (unsigned long long)req_id);
+        if (r->status != HPT_OK) return req_status(*r);
+        if (!r->out_lib) return fail(HPT_ERR_INVALID_ARG, "request %llu has no library-owned output", (unsigned long long)req_id);
+        src = r->out_lib;
+        n = r->out_bytes;
+    }
+    if (bytes < n) return fail(HPT_ERR_INVALID_ARG, "bytes %zu < %zu", bytes, n);
+    // the output stays until hpt_request_release, which this copy precedes on the same stream
+    CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, ctx->ostream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->ostream));
+    return HPT_OK;
+}
+
+extern "C" hpt_status hpt_request_release(hpt_ctx *ctx, uint64_t req_id)
+{
+    g_err.clear();
+    hpt_status st = check_ctx(ctx);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto r = find_req(ctx, req_id);
+    if (!r) return fail(HPT_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+    if (!r->done) return fail(HPT_ERR_BUSY, "request %llu not done (cancel it first)", (unsigned long long)req_id);
+    if (r->out_lib) CUDA_TRY(cudaFreeAsync(r->out_lib, ctx->ostream));
+    r->out_lib = nullptr;
+    ctx->reqs.erase(req_id);
+    ctx->scv.notify_all();
+    return HPT_OK;
+}
+
 // ------------------------------------------------------------ accessors for hpt_static.cu
 namespace hpt {
 hpt_status internal_make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, void *out, size_t out_bytes,
@@ -1764,9 +1992,11 @@ hpt_status internal_make_job(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_d
     return make_job(ctx, scene_id, desc, out, out_bytes, J, nullptr);
 }
 int internal_ctx_device(const hpt_ctx *ctx) { return ctx->device; }
-int internal_grid(const hpt_ctx *ctx, int prec, int which)
+void internal_grids(hpt_ctx *ctx, int prec, int &grid_trace, int &grid_shade)
 {
-    return which == 0 ? ctx->grid_trace[prec] : ctx->grid_shade[prec];
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    grid_trace = ctx->grid_trace[prec];
+    grid_shade = ctx->grid_shade[prec];
 }
 hpt_status internal_fail(hpt_status st, const char *msg) { return fail(st, "%s", msg); }
 hpt_status internal_check(hpt_ctx *ctx)

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libhpt.so")
 
 HPT_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY",
-                -6: "NOT_FOUND", -7: "UNSUPPORTED", -8: "DEVICE"}
+                -6: "NOT_FOUND", -7: "UNSUPPORTED", -8: "DEVICE", -9: "CANCELLED"}
+CTX_NO_GRAPHS, CTX_FAIL_SERVING_WAVES = 1, 2
 PREC_FP64, PREC_DF32 = 0, 1
 NCOUNTERS = 8
 COUNTER_NAMES = ["samples", "rays", "box_tests", "tri_tests", "refines", "fp64_fallbacks", "shadow_rays", "bounces"]
@@ -26,7 +27,7 @@ SYMBOLS = ["hpt_create", "hpt_destroy", "hpt_last_error", "hpt_scene_upload", "h
            "hpt_trace", "hpt_trace_host", "hpt_sync", "hpt_trace_counters", "hpt_submit", "hpt_poll", "hpt_wait",
            "hpt_request_times", "hpt_trace_fixed_scratch", "hpt_autotune", "hpt_trace_timed", "hpt_grf_build",
            "hpt_asm_propagate", "hpt_cache_bake", "hpt_scene_set_cache", "hpt_phase_encode",
-           "hpt_probe_peaks", "hpt_cache_upload"]
+           "hpt_probe_peaks", "hpt_cache_upload", "hpt_cancel", "hpt_request_output", "hpt_request_release"]
 
 
 # kernel kinds of hpt_trace_timed, in the order of HPT_K_GEN .. HPT_K_ACCUM
@@ -110,6 +111,9 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
     lib.hpt_wait.argtypes = [vp, C.c_uint64, C.c_uint32]
     lib.hpt_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double)]
+    lib.hpt_cancel.argtypes = [vp, C.c_uint64]
+    lib.hpt_request_output.argtypes = [vp, C.c_uint64, vp, C.c_size_t]
+    lib.hpt_request_release.argtypes = [vp, C.c_uint64]
     lib.hpt_trace_fixed_scratch.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
     lib.hpt_autotune.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), C.POINTER(C.c_int32)]
     for name in SYMBOLS:
@@ -159,10 +163,10 @@ class Context:
     """One library context on one CUDA device (owns scenes and launch slots)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, graphs: bool = True,
-                 max_queue: int = 0):
+                 max_queue: int = 0, flags: int = 0):
         self.lib = load_library()
         self.h = C.c_void_p()
-        desc = CtxDesc(hbm_budget_bytes, max_inflight, 0 if graphs else 1, max_queue, 0)
+        desc = CtxDesc(hbm_budget_bytes, max_inflight, (0 if graphs else CTX_NO_GRAPHS) | int(flags), max_queue, 0)
         _check(self.lib.hpt_create(C.byref(self.h), int(device), C.byref(desc)))
         self.device = device
 
@@ -379,6 +383,23 @@ class Context:
         t = (C.c_double * 3)()
         _check(self.lib.hpt_request_times(self.h, C.c_uint64(rid), t))
         return tuple(t)
+
+    def cancel(self, rid: int):
+        _check(self.lib.hpt_cancel(self.h, C.c_uint64(rid)))
+
+    def request_output(self, rid: int, dst):
+        """Copy a finished request's library-owned output into dst (a numpy complex64 array or a
+        contiguous torch tensor, host or device, of at least the output's size)."""
+        if isinstance(dst, np.ndarray):
+            assert dst.flags.c_contiguous
+            ptr, n = dst.ctypes.data, dst.nbytes
+        else:
+            assert dst.is_contiguous()
+            ptr, n = dst.data_ptr(), dst.numel() * dst.element_size()
+        _check(self.lib.hpt_request_output(self.h, C.c_uint64(rid), C.c_void_p(ptr), n))
+
+    def request_release(self, rid: int):
+        _check(self.lib.hpt_request_release(self.h, C.c_uint64(rid)))
 
 
 def _dev_buffer(out, r):
