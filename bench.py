@@ -75,6 +75,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-counters", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--cfg4-requests", type=int, default=2000, help="requests of the config-4 serving stream")
+    p.add_argument("--serving-sweep", default="",
+                   help="comma-separated offered rates (req/s): run only the config-4 bounded-admission sweep")
+    p.add_argument("--sweep-requests", type=int, default=200)
     p.add_argument("--no-optics", action="store_true")
     p.add_argument("--workload", default="cfg2", choices=list(WORKLOADS),
                    help="cfg2 = the headline workload; the others are smaller cases of the same kernels for profiling")
@@ -220,49 +225,6 @@ def precision_report(U, ref):
             "max_phase_rad": max(x["max_phase_rad"] for x in out), "pixels": int(U.shape[2])}
 
 
-def _pose_T(dx, dy, dz):
-    """Rigid world -> hologram transform of an eye offset (dx, dy) and an axial focus shift dz."""
-    T = np.eye(4)
-    T[0, 3], T[1, 3], T[2, 3] = -dx, -dy, -dz
-    return T
-
-
-def serve(ctx, hpt, S, requests, rate, seed):
-    """Submit requests with Poisson arrivals at 'rate' per second; returns latency statistics.
-    requests: list of (scene id, render, precision, output tensor)."""
-    rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / rate, len(requests))
-    ctx.sync()
-    ids, done, rejected, t0 = [], [], 0, time.perf_counter()
-    t_next = t0
-    for (sid, r, prec, out), g in zip(requests, gaps):
-        t_next += g
-        dt = t_next - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        try:
-            ids.append(ctx.submit(sid, r, out, precision=prec))
-            done.append(r)
-        except hpt.HptError as e:
-            if e.status != -5:           # only HPT_ERR_BUSY (the bounded queue is full) is expected
-                raise
-            rejected += 1
-    for i in ids:
-        ctx.wait(i, 600000)
-    if not ids:
-        return {"requests": len(requests), "rejected": rejected, "offered_rate_per_s": rate}
-    times = np.array([ctx.request_times(i) for i in ids]) / 1e6
-    lat = times[:, 2] - times[:, 0]
-    span = times[:, 2].max() - times[:, 0].min()
-    holos = sum(r.K for r in done)
-    return {"requests": len(requests), "rejected": rejected, "offered_rate_per_s": rate,
-            "completed_rate_per_s": len(ids) / span, "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s": float(np.mean(times[:, 1] - times[:, 0])),
-            "p99_queue_s": float(np.percentile(times[:, 1] - times[:, 0], 99)),
-            "holograms_per_s": holos / span, "path_samples_per_s": sum(r.path_samples() for r in done) / span,
-            "span_s": float(span)}
-
-
 def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
     """The wave-optics steps around the tracer on the headline output: the K GRF phase maps of
     Eq. 4 (4096 x 2048 grid of the SLM pitch), the angular-spectrum propagation of all
@@ -326,65 +288,113 @@ def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
     }
 
 
-def _mixed_requests(hpt, S, sid_cfg1, sid_cfg0, n, seed):
-    """n requests following the serving recipe (scenes, poses, focal depths, SLM sizes, spp, K),
-    scaled to 512x512 and 1920x1080 SLMs and spp <= 64 so that a stream ends in seconds."""
+def serve_owned(ctx, hpt, requests, rate, seed):
+    """Submit requests with Poisson arrivals at 'rate' per second, outputs owned by the library
+    (allocated at admission by free HBM), and release each as it finishes.  requests: list of
+    (scene id, render).  Returns latency and throughput statistics of the completed requests."""
     rng = np.random.default_rng(seed)
-    z_med = {sid_cfg0: 7.5e-3, sid_cfg1: 17.5e-3}
-    mix = []
-    for k in range(n):
-        sid = sid_cfg1 if rng.random() < 0.6 else sid_cfg0
-        big = rng.random() < 0.4
-        W, H = (1920, 1080) if big else (512, 512)
-        spp = int(rng.choice([16, 32, 64]))
-        K = int(rng.choice([1, 4, 8]))
-        dx, dy = rng.uniform(-5e-3, 5e-3, 2)
-        df = rng.uniform(5e-3, 30e-3)
-        if sid == sid_cfg1:
-            r = S.config1_render(W=W, H=H, spp=spp, K=K, seed=100 + k, T=_pose_T(dx, dy, z_med[sid] - df))
-        else:
-            r = S.config0_render(W=W, H=H, spp=spp, K=K, seed=100 + k, pitch=6.4e-6,
-                                 T=_pose_T(dx * 0.1, dy * 0.1, 0.0))
-        mix.append((sid, r, hpt.PREC_DF32, hpt.alloc_output(r)))
-    return mix
-
-
-SWEEP_REQUESTS = 96
-MIX_DESC = ("Poisson arrivals; scenes cfg1 (60%) / cfg0, SLM 512x512 or 1920x1080, spp in {16,32,64}, "
-            "K in {1,4,8}, eye offsets U[-5,5] mm, focal depth U[5,30] mm")
-
-
-def run_serving(ctx, hpt, S, sid_cfg1, sid_cfg0):
-    """(a) headline requests (1080p RGB 64 spp depth 4 K=8) at 2 req/s, near the device's capacity;
-    (b) a mixed request stream at 40 req/s (unbounded queue); (c) the same mix with bounded
-    admission (8 requests on the device, 8 waiting; a submission beyond that is rejected and
-    counted) at increasing offered rates: the highest rate sustained is the highest with no
-    rejection and a p99 wait for admission under 1 s."""
-    head = [(sid_cfg1, S.config2_render(seed=10 + k), hpt.PREC_DF32, None) for k in range(6)]
-    head = [(sid, r, prec, hpt.alloc_output(r)) for sid, r, prec, _ in head]
-    a = serve(ctx, hpt, S, head, 2.0, 7)
-    a["workload"] = "6 requests of the headline render (1920x1080 RGB, 64 spp, depth 4, K=8), Poisson 2 req/s"
-    del head
-    b = serve(ctx, hpt, S, _mixed_requests(hpt, S, sid_cfg1, sid_cfg0, 24, 4242), 40.0, 8)
-    b["workload"] = "24 requests at 40 req/s, " + MIX_DESC
+    gaps = rng.exponential(1.0 / rate, len(requests))
     ctx.sync()
-    bounded = hpt.Context(ctx.device, max_inflight=8, max_queue=8)
+    outstanding, done, rejected = {}, [], 0
+
+    def reap(block):
+        for i in list(outstanding):
+            if block:
+                ctx.wait(i, 600000)
+            elif not ctx.poll(i):
+                continue
+            done.append((ctx.request_times(i), outstanding.pop(i)))
+            ctx.request_release(i)
+
+    t_next = time.perf_counter()
+    for (sid, r), g in zip(requests, gaps):
+        t_next += g
+        while True:
+            dt = t_next - time.perf_counter()
+            if dt <= 0:
+                break
+            reap(False)
+            time.sleep(min(dt, 0.004))
+        try:
+            outstanding[ctx.submit(sid, r, None, precision=hpt.PREC_DF32)] = r
+        except hpt.HptError as e:
+            if e.status != -5:           # only HPT_ERR_BUSY (the bounded queue is full) is expected
+                raise
+            rejected += 1
+    reap(True)
+    if not done:
+        return {"requests": len(requests), "rejected": rejected, "offered_rate_per_s": rate}
+    times = np.array([t for t, _ in done]) / 1e6
+    rs = [r for _, r in done]
+    lat = times[:, 2] - times[:, 0]
+    queue = times[:, 1] - times[:, 0]
+    span = times[:, 2].max() - times[:, 0].min()
+    by_size = {}
+    for (W, H) in sorted({(r.W, r.H) for r in rs}):
+        l = lat[[k for k, r in enumerate(rs) if (r.W, r.H) == (W, H)]]
+        by_size[f"{W}x{H}"] = {"completed": int(len(l)), "p50_latency_s": float(np.percentile(l, 50)),
+                               "p99_latency_s": float(np.percentile(l, 99))}
+    return {"requests": len(requests), "rejected": rejected, "completed": len(done), "offered_rate_per_s": rate,
+            "completed_rate_per_s": len(done) / span, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "max_latency_s": float(lat.max()),
+            "p50_queue_s": float(np.percentile(queue, 50)), "p99_queue_s": float(np.percentile(queue, 99)),
+            "holograms_per_s": sum(r.K for r in rs) / span,
+            "path_samples_per_s": sum(r.path_samples() for r in rs) / span, "span_s": float(span),
+            "latency_by_slm": by_size}
+
+
+CFG4_DESC = ("Poisson arrivals; workload drawn uniformly from configs 0-3 (scenes of 4, 23k and 185k triangles, the "
+             "185k-triangle scene with its 128^3 ambient cache; each config's pitch, wavelengths and depth), SLM "
+             "512x512 / 1920x1080 / 3840x2160, spp in {16,32,64,128,256}, K in {1,4,8}, eye offsets U[-5,5] mm, "
+             "focal depth U[5,30] mm; scenes and cache resident; outputs allocated by the library at admission")
+
+
+def cfg4_context(hpt, S, device, max_inflight=8, max_queue=8):
+    ctx = hpt.Context(device, max_inflight=max_inflight, max_queue=max_queue)
+    sids = {"cfg0": ctx.upload_scene(S.config0_scene()), "cfg1": ctx.upload_scene(S.config1_scene()),
+            "cfg3": ctx.upload_scene(S.config3_scene())}
+    return ctx, sids
+
+
+def run_serving(ctx, hpt, S, sid_cfg1, batched_holos, plain_holos, n_cfg4=2000):
+    """(a) the headline request (1080p RGB 64 spp depth 4 K=8) offered above the device's capacity:
+    the served throughput beside the batched and plain forms; (b) the serving workload of config 4:
+    a seeded stream of n_cfg4 requests at 40 req/s with bounded admission (8 requests on the
+    device, 8 waiting; a submission beyond that is rejected and counted)."""
+    head = [(sid_cfg1, S.config2_render(seed=10 + k)) for k in range(12)]
+    a = serve_owned(ctx, hpt, head, 8.0, 7)
+    a["workload"] = "12 requests of the headline render (1920x1080 RGB, 64 spp, depth 4, K=8), Poisson 8 req/s"
+    a["batched_holograms_per_s"] = batched_holos
+    a["plain_fp64_holograms_per_s"] = plain_holos
+    ctx.sync()
+    bctx, sids = cfg4_context(hpt, S, ctx.device)
+    try:
+        reqs = [(sids[key], r) for key, r in S.config4_requests(n_cfg4, 4242)]
+        b = serve_owned(bctx, hpt, reqs, 40.0, 8)
+        b.update({"max_inflight": 8, "max_queue": 8, "workload": f"{n_cfg4} requests at 40 req/s, " + CFG4_DESC})
+        bctx.sync()
+    finally:
+        bctx.close()
+    return {"headline_at_capacity": a, "cfg4": b}
+
+
+def run_serving_sweep(hpt, S, device, n, rates):
+    """The config-4 stream with bounded admission at increasing offered rates: the highest rate
+    sustained is the highest with no rejection and a p99 wait for admission under 1 s."""
+    ctx, sids = cfg4_context(hpt, S, device)
     sweep, best = [], 0.0
     try:
-        s1, s0 = bounded.upload_scene(S.config1_scene()), bounded.upload_scene(S.config0_scene())
-        reqs = _mixed_requests(hpt, S, s1, s0, SWEEP_REQUESTS, 5000)     # the same stream at every rate
-        for k, rate in enumerate((10.0, 15.0, 20.0, 25.0, 30.0, 40.0)):
-            res = serve(bounded, hpt, S, reqs, rate, 9 + k)
+        for k, rate in enumerate(rates):
+            reqs = [(sids[key], r) for key, r in S.config4_requests(n, 5000 + k)]
+            res = serve_owned(ctx, hpt, reqs, rate, 9 + k)
             sweep.append(res)
             if res["rejected"] == 0 and res.get("p99_queue_s", 1e9) <= 1.0:
                 best = max(best, rate)
-        del reqs
-        bounded.sync()
+        ctx.sync()
     finally:
-        bounded.close()
-    return {"headline_requests": a, "mixed_stream": b,
-            "bounded_sweep": {"max_inflight": 8, "max_queue": 8, "requests_per_rate": SWEEP_REQUESTS, "workload": MIX_DESC,
-                              "rates": sweep, "max_sustained_rate_per_s": best}}
+        ctx.close()
+    return {"max_inflight": 8, "max_queue": 8, "requests_per_rate": n, "workload": CFG4_DESC, "rates": sweep,
+            "max_sustained_rate_per_s": best}
 
 
 def run_reference(args):
@@ -425,6 +435,11 @@ def main():
     import torch
     from paper_2606_14173_gb300 import build as pbuild, hpt, scenes as S
 
+    if args.serving_sweep:
+        pbuild.build()
+        res = run_serving_sweep(hpt, S, 0, args.sweep_requests, [float(x) for x in args.serving_sweep.split(",")])
+        print(json.dumps({"serving_sweep": res}), flush=True)
+        return
     world, rank, local = dist_init()
     torch.cuda.set_device(local)
     if rank == 0 or world > 1:
@@ -437,6 +452,9 @@ def main():
     make_render = getattr(S, render_fn)
     r = make_render(seed=replica_seed(rank), **wl_over)
     samples_per_step = r.path_samples()
+    # launch shape (wave size, lanes, grid sizes) chosen by the library's autotuner on a band of
+    # this render, before any timing; kept for the scene's size class
+    tuning = None if args.no_autotune else ctx.autotune(sid, r, precision=hpt.PREC_DF32)
     out = hpt.alloc_output(r)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     # all work on one dedicated stream: the legacy default stream serialises with the library's
@@ -560,9 +578,9 @@ def main():
         ctx.sync()
 
     serving = None
-    if not args.no_serving and args.workload == "cfg2":
-        sid0 = ctx.upload_scene(S.config0_scene())
-        serving = run_serving(ctx, hpt, S, sid, sid0)
+    if not args.no_serving and args.workload == "cfg2" and rank == 0:
+        serving = run_serving(ctx, hpt, S, sid, holo_per_s, plain["holograms_per_s"] if plain else None,
+                              args.cfg4_requests)
         ctx.sync()
 
     cpu = None
@@ -603,7 +621,7 @@ def main():
                 "idle_ms_per_step": (total_ms - sum(launch_ms)) / args.steps,
                 "gaps_ms": [round(g, 3) for g in gaps_ms[0]],
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * sum(n for _, n in kt.values()),
-                "graph_launches": args.steps, "roofline": roofline, "optics": optics, "serving": serving, "precision": precision,
+                "graph_launches": args.steps, "autotune": tuning, "roofline": roofline, "optics": optics, "serving": serving, "precision": precision,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

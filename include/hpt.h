@@ -220,13 +220,32 @@ hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_des
                            void *out_dev, size_t out_bytes, float kernel_ms[HPT_NKERNELS],
                            uint32_t launches[HPT_NKERNELS]);
 
-/* Choose the context's wave size (paths per wave: 1M .. 16M, within half of the free HBM) by
- * timing hpt_trace of a 128-row band of 'desc' (spp capped at 32) for each candidate; keeps the
- * fastest (a larger wave must win by more than 2 %), reallocates the wave state and drops the
- * captured frames.  Synchronous; *paths_per_wave receives the choice.  Results of later traces
- * do not depend on the wave size. */
-hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
-                        int32_t *paths_per_wave);
+/* Launch-shape autotuner (the paper has no counterpart).  Times hpt_trace of a band of 'desc'
+ * (its first rows, about 50 M path samples, all wavelengths, spp and K as given) under candidate
+ * launch shapes and keeps the fastest, by coordinate descent from the current shape:
+ *   paths_per_wave       wave size, 2 M .. 16 M paths (within half of the free HBM);
+ *   lanes                wave lanes (path-state sets on their own streams), 1 .. 4;
+ *   trace_blocks_per_sm  resident blocks of the trace kernel x 1, 2 or 4 per SM in its grid;
+ *   shade_blocks_per_sm  the same for the shading kernels.
+ * A candidate replaces the current choice only when it is faster by more than 1 %.  The result
+ * is applied to the context (reallocating the wave state and dropping captured frames when the
+ * wave size or lane count changes) and kept for the scene's size class (triangle count < 4 k,
+ * < 64 k, < 1 M, larger); later hpt_trace / hpt_trace_host calls on a scene of a tuned class
+ * switch to that class's shape first.  Results of traces do not depend on the launch shape.
+ * Synchronous; *out receives the choice (out may be NULL).  Serving waves keep their own shape. */
+enum { HPT_SCENE_CLASSES = 4 };
+typedef struct {
+    int32_t paths_per_wave;
+    int32_t lanes;
+    int32_t trace_blocks_per_sm;
+    int32_t shade_blocks_per_sm;
+    int32_t scene_class;
+    int32_t candidates;        /* launch shapes timed */
+    double band_ms;            /* band time of the choice (best of the timed repetitions) */
+    double band_ms_start;      /* band time of the shape the context had before the call */
+    int64_t band_path_samples; /* path samples of the band */
+} hpt_tuning;
+hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, hpt_tuning *out);
 
 /* ---- wave optics around the tracer: GRF phase maps and angular-spectrum propagation ---- */
 /* Eq. 4 (Sec. 4.3): for m = hologram_offset .. hologram_offset + K - 1, the band-limited

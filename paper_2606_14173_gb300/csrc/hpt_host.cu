@@ -262,12 +262,20 @@ struct hpt_ctx {
     int device = 0;
     int sm_count = 0;
     int grid_trace[2] = {1, 1}, grid_shade[2] = {1, 1};
+    int occ_trace[2] = {1, 1}, occ_shade[2] = {1, 1};   // resident blocks per SM of the two kernels
+    int lanes = HPT_LANES;                               // wave lanes of a trace (1 .. HPT_MAX_LANES)
+    int trace_mult = 1, shade_mult = 1;                  // grid = SMs x resident blocks x mult
+    struct Shape {
+        int cap, lanes, tm, sm;
+    };
+    Shape tuned[HPT_SCENE_CLASSES]{};                    // hpt_autotune results per scene-size class
+    bool tuned_valid[HPT_SCENE_CLASSES] = {};
     // path state of one wave (capacity paths), all wave work runs on wstream
     PathBufs pb{};
     void *pb_arena = nullptr;
     // wave lanes: consecutive waves of a trace rotate over lane 0 (pb, d_scr, wstream) and the
     // extra lanes below, so that one wave's kernels fill the others' launch gaps and tails
-    static constexpr int EXTRA_LANES = HPT_LANES - 1;
+    static constexpr int EXTRA_LANES = HPT_MAX_LANES - 1;
     void *pb_arena_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
     PathBufs pb_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1]{};
     SlotScratch *d_scr_x[EXTRA_LANES > 0 ? EXTRA_LANES : 1] = {};
@@ -281,7 +289,8 @@ struct hpt_ctx {
     cudaStream_t slane_stream[HPT_LANES] = {};
     cudaEvent_t slane_ev[HPT_LANES] = {};   // end of the lane's latest wave
     int sched_next = 0;
-    int capacity = 1 << 23;   // paths per wave (~1.7 GB of path state)
+    int capacity = 1 << 23;   // paths per wave of a trace (~1.7 GB of path state per lane)
+    int sched_capacity = 1 << 23;   // paths per serving wave (fixed when the context is created)
     int debug_waves = 0;
     // captured frames of hpt_trace, keyed by what fixes the launch sequence
     // A captured frame reads its job table from d_table; each replay first copies the
@@ -380,10 +389,13 @@ extern "C" hpt_status hpt_create(hpt_ctx **out, int device, const hpt_ctx_desc *
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
     for (int prec = 0; prec < 2; ++prec) {
         CUDA_TRY(wave_preload(prec));   // all wave kernels loaded now, not at a first launch
-        ctx->grid_trace[prec] = ctx->sm_count * wave_occupancy(prec, 0);
-        ctx->grid_shade[prec] = ctx->sm_count * wave_occupancy(prec, 1);
+        ctx->occ_trace[prec] = wave_occupancy(prec, 0);
+        ctx->occ_shade[prec] = wave_occupancy(prec, 1);
+        ctx->grid_trace[prec] = ctx->sm_count * ctx->occ_trace[prec];
+        ctx->grid_shade[prec] = ctx->sm_count * ctx->occ_shade[prec];
     }
     if (const char *e = getenv("HPT_WAVE_PATHS")) ctx->capacity = std::max(1 << 12, std::min(atoi(e), 1 << 26));
+    ctx->sched_capacity = ctx->capacity;
     if (const char *e = getenv("HPT_DEBUG_WAVES")) ctx->debug_waves = atoi(e);
     if (desc) ctx->flags = desc->flags;
     if (desc && (desc->flags & HPT_CTX_NO_GRAPHS)) ctx->use_graphs = false;
@@ -931,7 +943,7 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
     if (ctx->pb_arena) return HPT_OK;
     const size_t B = (size_t)ctx->capacity;
     CUDA_TRY(cudaMalloc(&ctx->pb_arena, B * path_bytes() + 64 * 256));
-    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+    for (int l = 0; l < ctx->lanes - 1; ++l) {
         cudaError_t e = cudaMalloc(&ctx->pb_arena_x[l], B * path_bytes() + 64 * 256);
         if (e != cudaSuccess) {
             cudaFree(ctx->pb_arena);
@@ -952,7 +964,7 @@ static hpt_status ensure_paths(hpt_ctx *ctx)
 static hpt_status ensure_sched_paths(hpt_ctx *ctx)
 {
     if (ctx->spb_arena[0]) return HPT_OK;
-    const size_t B = (size_t)ctx->capacity;
+    const size_t B = (size_t)ctx->sched_capacity;
     for (int l = 0; l < HPT_LANES; ++l) {
         if (!ctx->slane_stream[l]) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->slane_stream[l], cudaStreamNonBlocking));
         if (!ctx->slane_ev[l]) CUDA_TRY(cudaEventCreateWithFlags(&ctx->slane_ev[l], cudaEventDisableTiming));
@@ -984,9 +996,9 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
     memset(&wd, 0, sizeof wd);
     int max_depth = 1;
     hpt_status st = HPT_OK;
-    // waves rotate over HPT_LANES lanes (path state, scratch, stream); the extra lanes fork from
+    // waves rotate over ctx->lanes lanes (path state, scratch, stream); the extra lanes fork from
     // ws at the start and join ws at the end.  Per-kernel timing keeps one lane.
-    const int lanes = ctx->timer == nullptr ? HPT_LANES : 1;
+    const int lanes = ctx->timer == nullptr ? ctx->lanes : 1;
     int n_waves = 0;
     bool forked = false;
     auto mark = [&](int kind) -> cudaError_t {
@@ -1121,6 +1133,8 @@ static void free_frame(hpt_ctx::FrameGraph &g)
     g = hpt_ctx::FrameGraph();
 }
 
+static hpt_status apply_tuned(hpt_ctx *ctx, const SceneRec *rec);
+
 static hpt_status run_graph(hpt_ctx *ctx, const DevJob &J, int prec, cudaStream_t user)
 {
     hpt_status st = ensure_paths(ctx);
@@ -1200,9 +1214,12 @@ extern "C" hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_rende
     if (st) return st;
     if (!out_dev) return fail(HPT_ERR_INVALID_ARG, "out_dev is NULL");
     DevJob J;
-    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, nullptr);
+    SceneRec *rec = nullptr;
+    st = make_job(ctx, scene_id, desc, out_dev, out_bytes, J, &rec);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    st = apply_tuned(ctx, rec);
+    if (st) return st;
     nvtxRangePushA("hpt_trace frame");
     st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, (cudaStream_t)stream)
                                                   : run_jobs(ctx, &J, 1, desc->precision, false, (cudaStream_t)stream);
@@ -1218,11 +1235,14 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
     if (st) return st;
     if (!out_host || !desc) return fail(HPT_ERR_INVALID_ARG, "out_host or desc is NULL");
     DevJob J;
-    st = make_job(ctx, scene_id, desc, nullptr, 0, J, nullptr);
+    SceneRec *rec = nullptr;
+    st = make_job(ctx, scene_id, desc, nullptr, 0, J, &rec);
     if (st) return st;
     size_t need = (size_t)8 * desc->n_lambda * desc->K * (size_t)desc->W * desc->H;
     if (out_bytes < need) return fail(HPT_ERR_INVALID_ARG, "out_bytes %zu < %zu", out_bytes, need);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    st = apply_tuned(ctx, rec);
+    if (st) return st;
     if (ctx->host_out_bytes < need) {
         CUDA_TRY(cudaDeviceSynchronize());
         if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
@@ -1459,85 +1479,148 @@ static void drop_graphs(hpt_ctx *ctx)
     ctx->graphs.clear();
 }
 
-static hpt_status set_capacity(hpt_ctx *ctx, int cap)
+static int scene_class(int n_tris)
 {
-    if (cap == ctx->capacity && ctx->pb_arena) return HPT_OK;
-    CUDA_TRY(cudaStreamSynchronize(ctx->wstream));
-    drop_graphs(ctx);
-    CUDA_TRY(cudaDeviceSynchronize());
-    if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
-    ctx->pb_arena = nullptr;
-    for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
-        if (ctx->pb_arena_x[l]) CUDA_TRY(cudaFree(ctx->pb_arena_x[l]));
-        ctx->pb_arena_x[l] = nullptr;
-    }
-    for (int l = 0; l < HPT_LANES; ++l) {
-        if (ctx->spb_arena[l]) CUDA_TRY(cudaFree(ctx->spb_arena[l]));
-        ctx->spb_arena[l] = nullptr;
-    }
-    ctx->capacity = cap;
-    return ensure_paths(ctx);
+    return n_tris < (1 << 12) ? 0 : n_tris < (1 << 16) ? 1 : n_tris < (1 << 20) ? 2 : 3;
 }
 
-extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
-                                   int32_t *paths_per_wave)
+// Switch the trace launch shape: wave size, lanes and grid multipliers.  Caller holds ctx->mu.
+static hpt_status set_shape(hpt_ctx *ctx, int cap, int lanes, int tm, int sm)
+{
+    const bool realloc = cap != ctx->capacity || lanes != ctx->lanes || !ctx->pb_arena;
+    if (realloc || tm != ctx->trace_mult || sm != ctx->shade_mult) drop_graphs(ctx);   // frames embed the shape
+    if (realloc) {
+        CUDA_TRY(cudaDeviceSynchronize());   // waves in flight use the wave state
+        if (ctx->pb_arena) CUDA_TRY(cudaFree(ctx->pb_arena));
+        ctx->pb_arena = nullptr;
+        for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) {
+            if (ctx->pb_arena_x[l]) CUDA_TRY(cudaFree(ctx->pb_arena_x[l]));
+            ctx->pb_arena_x[l] = nullptr;
+        }
+        ctx->capacity = cap;
+        ctx->lanes = lanes;
+    }
+    ctx->trace_mult = tm;
+    ctx->shade_mult = sm;
+    for (int prec = 0; prec < 2; ++prec) {
+        ctx->grid_trace[prec] = ctx->sm_count * ctx->occ_trace[prec] * tm;
+        ctx->grid_shade[prec] = ctx->sm_count * ctx->occ_shade[prec] * sm;
+    }
+    return realloc ? ensure_paths(ctx) : HPT_OK;
+}
+
+// the tuned shape of the scene's size class, if hpt_autotune recorded one; caller holds ctx->mu
+static hpt_status apply_tuned(hpt_ctx *ctx, const SceneRec *rec)
+{
+    const int c = scene_class(rec->dev.n_tris);
+    if (!ctx->tuned_valid[c]) return HPT_OK;
+    const hpt_ctx::Shape &t = ctx->tuned[c];
+    if (t.cap == ctx->capacity && t.lanes == ctx->lanes && t.tm == ctx->trace_mult && t.sm == ctx->shade_mult &&
+        ctx->pb_arena)
+        return HPT_OK;
+    return set_shape(ctx, t.cap, t.lanes, t.tm, t.sm);
+}
+
+extern "C" hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc, hpt_tuning *out)
 {
     g_err.clear();
     hpt_status st = check_ctx(ctx);
     if (st) return st;
-    if (!desc || !paths_per_wave) return fail(HPT_ERR_INVALID_ARG, "desc or paths_per_wave is NULL");
+    if (!desc) return fail(HPT_ERR_INVALID_ARG, "desc is NULL");
     hpt_render_desc band = *desc;
-    band.H = std::min(desc->H, 128);
-    band.spp = std::min(desc->spp, 32);
+    const double per_row = (double)desc->W * std::max(desc->n_lambda, 1) * std::max(desc->spp, 1);
+    band.H = (int)std::min<double>(desc->H, std::max(1.0, std::ceil(50e6 / per_row)));
     DevJob J;
-    st = make_job(ctx, scene_id, &band, nullptr, 0, J, nullptr);
+    SceneRec *rec = nullptr;
+    st = make_job(ctx, scene_id, &band, nullptr, 0, J, &rec);
     if (st) return st;
     const size_t out_b = (size_t)8 * band.n_lambda * band.K * (size_t)band.W * band.H;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    void *out = nullptr;
-    CUDA_TRY(cudaMalloc(&out, out_b));
-    J.out = (float2 *)out;
-    const int old = ctx->capacity;
+    void *dout = nullptr;
+    CUDA_TRY(cudaMalloc(&dout, out_b));
+    J.out = (float2 *)dout;
     size_t fr = 0, tot = 0;
-    CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t avail = fr + (ctx->pb_arena ? (size_t)HPT_LANES * ctx->capacity * path_bytes() : 0);
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    int best = old;
-    double best_rate = -1.0;
-    const int cands[] = {1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24};
-    for (int cap : cands) {
-        if ((size_t)HPT_LANES * cap * path_bytes() > avail / 2 || cap < J.spp) continue;
-        st = set_capacity(ctx, cap);
-        if (st) break;
-        float best_ms = 1e30f;
-        for (int rep = 0; rep < 3 && !st; ++rep) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMemGetInfo(&fr, &tot);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(dout);
+        return fail(HPT_ERR_CUDA, "autotune set-up: %s", cudaGetErrorString(ce));
+    }
+    const size_t avail = fr + (ctx->pb_arena ? (size_t)ctx->lanes * ctx->capacity * path_bytes() : 0);
+    hpt_ctx::Shape cur = {ctx->capacity, ctx->lanes, ctx->trace_mult, ctx->shade_mult};
+    const hpt_ctx::Shape start = cur;
+    int n_cand = 0;
+    auto fits = [&](const hpt_ctx::Shape &x) {
+        return (size_t)x.lanes * x.cap * path_bytes() <= avail / 2 && x.cap >= J.spp;
+    };
+    // band time of one shape: three runs, the first a warm-up, the best of the other two
+    auto measure = [&](const hpt_ctx::Shape &x, double &ms_out) -> hpt_status {
+        hpt_status s2 = set_shape(ctx, x.cap, x.lanes, x.tm, x.sm);
+        if (s2) return s2;
+        ++n_cand;
+        double best = 1e30;
+        for (int rep = 0; rep < 3; ++rep) {
             CUDA_TRY(cudaEventRecord(e0, ctx->wstream));
-            st = run_jobs(ctx, &J, 1, band.precision, false, ctx->wstream);
+            s2 = run_jobs(ctx, &J, 1, band.precision, false, ctx->wstream);
+            if (s2) return s2;
             CUDA_TRY(cudaEventRecord(e1, ctx->wstream));
             CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.0f;
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) best_ms = std::min(best_ms, ms);
+            if (rep > 0) best = std::min(best, (double)ms);
         }
-        if (st) break;
-        const double rate = (double)band.n_lambda * band.W * band.H * band.spp / best_ms;
-        if (rate > best_rate * 1.02) {   // prefer the smaller wave unless the larger is clearly faster
-            best_rate = rate;
-            best = cap;
+        ms_out = best;
+        return HPT_OK;
+    };
+    double best_ms = 0.0, start_ms = 0.0;
+    if (!fits(cur)) cur.cap = std::max(J.spp, 1 << 21);
+    st = measure(cur, best_ms);
+    start_ms = best_ms;
+    auto consider = [&](hpt_ctx::Shape x) {
+        if (st || !fits(x)) return;
+        if (x.cap == cur.cap && x.lanes == cur.lanes && x.tm == cur.tm && x.sm == cur.sm) return;
+        double ms = 0.0;
+        st = measure(x, ms);
+        if (!st && ms < best_ms * 0.99) {
+            best_ms = ms;
+            cur = x;
         }
-    }
+    };
+    const hpt_ctx::Shape c0 = cur;
+    for (int cap : {1 << 21, 1 << 22, 1 << 23, 1 << 24}) consider({cap, c0.lanes, c0.tm, c0.sm});
+    const hpt_ctx::Shape c1 = cur;
+    for (int lanes = 1; lanes <= HPT_MAX_LANES; ++lanes) consider({c1.cap, lanes, c1.tm, c1.sm});
+    const hpt_ctx::Shape c2 = cur;
+    for (int tm : {1, 2, 4}) consider({c2.cap, c2.lanes, tm, c2.sm});
+    const hpt_ctx::Shape c3 = cur;
+    for (int sm : {1, 2, 4}) consider({c3.cap, c3.lanes, c3.tm, sm});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(out);
+    cudaFree(dout);
     if (st) {
-        set_capacity(ctx, old);
-        return st;
+        const std::string msg = g_err;
+        set_shape(ctx, start.cap, start.lanes, start.tm, start.sm);
+        return fail(st, "%s", msg.c_str());
     }
-    st = set_capacity(ctx, best);
+    st = set_shape(ctx, cur.cap, cur.lanes, cur.tm, cur.sm);
     if (st) return st;
-    *paths_per_wave = best;
+    const int cls = scene_class(rec->dev.n_tris);
+    ctx->tuned[cls] = cur;
+    ctx->tuned_valid[cls] = true;
+    if (out) {
+        out->paths_per_wave = cur.cap;
+        out->lanes = cur.lanes;
+        out->trace_blocks_per_sm = ctx->occ_trace[band.precision] * cur.tm;
+        out->shade_blocks_per_sm = ctx->occ_shade[band.precision] * cur.sm;
+        out->scene_class = cls;
+        out->candidates = n_cand;
+        out->band_ms = best_ms;
+        out->band_ms_start = start_ms;
+        out->band_path_samples = (int64_t)band.n_lambda * band.W * (int64_t)band.H * band.spp;
+    }
     return read_status(ctx);
 }
 
@@ -1718,7 +1801,7 @@ static void sched_loop(hpt_ctx *ctx)
             if (!cand.empty() && slot_idx >= 0) {
                 ctx->status_slot_used[slot_idx] = true;
                 ctx->rr = (ctx->rr + 1) % std::max<size_t>(na, 1);
-                const long long share = std::max<long long>(1, (long long)ctx->capacity / (long long)cand.size());
+                const long long share = std::max<long long>(1, (long long)ctx->sched_capacity / (long long)cand.size());
                 for (auto &r : cand) {
                     long long take = std::max<long long>(1, share / r->job.spp);
                     take = std::min<long long>(take, r->job.n_items - r->next);
@@ -1848,7 +1931,7 @@ extern "C" hpt_status hpt_submit(hpt_ctx *ctx, uint64_t scene_id, const hpt_rend
     SceneRec *rec = nullptr;
     st = make_job(ctx, scene_id, desc, out_dev, out_dev ? out_bytes : 0, r->job, &rec);
     if (st) return st;
-    if (r->job.spp > ctx->capacity) return fail(HPT_ERR_UNSUPPORTED, "spp exceeds the wave capacity");
+    if (r->job.spp > ctx->sched_capacity) return fail(HPT_ERR_UNSUPPORTED, "spp exceeds the wave capacity");
     r->scene = rec;
     r->prec = desc->precision;
     r->out_bytes = (size_t)8 * desc->n_lambda * desc->K * (size_t)desc->W * desc->H;

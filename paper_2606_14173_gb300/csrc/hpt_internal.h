@@ -7,8 +7,9 @@ namespace hpt {
 
 constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
 #ifndef HPT_LANES
-#define HPT_LANES 3   // wave lanes of a trace (path-state sets rotating over streams)
+#define HPT_LANES 3   // wave lanes of a trace by default (path-state sets rotating over streams)
 #endif
+#define HPT_MAX_LANES 4   // most wave lanes a trace may use (hpt_autotune chooses 1 .. 4)
 #ifndef HPT_TSTACK
 #define HPT_TSTACK 32
 #endif

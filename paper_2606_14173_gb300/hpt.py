@@ -68,6 +68,12 @@ class RenderDesc(C.Structure):
                 ("grf_nx", C.c_int32), ("grf_ny", C.c_int32), ("omit_obliquity", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("paths_per_wave", C.c_int32), ("lanes", C.c_int32), ("trace_blocks_per_sm", C.c_int32),
+                ("shade_blocks_per_sm", C.c_int32), ("scene_class", C.c_int32), ("candidates", C.c_int32),
+                ("band_ms", C.c_double), ("band_ms_start", C.c_double), ("band_path_samples", C.c_int64)]
+
+
 class BakeDesc(C.Structure):
     _fields_ = [("res", C.c_int32), ("bmin", C.c_float * 3), ("bmax", C.c_float * 3), ("spp", C.c_int32),
                 ("max_depth", C.c_int32), ("seed", C.c_uint64)]
@@ -115,7 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.hpt_request_output.argtypes = [vp, C.c_uint64, vp, C.c_size_t]
     lib.hpt_request_release.argtypes = [vp, C.c_uint64]
     lib.hpt_trace_fixed_scratch.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), vp, C.c_size_t, vp]
-    lib.hpt_autotune.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), C.POINTER(C.c_int32)]
+    lib.hpt_autotune.argtypes = [vp, C.c_uint64, C.POINTER(RenderDesc), C.POINTER(Tuning)]
     for name in SYMBOLS:
         f = getattr(lib, name)
         if name not in ("hpt_destroy", "hpt_last_error"):
@@ -353,12 +359,13 @@ class Context:
                                           lam, float(pitch), float(z), _stream_ptr(stream)))
         return out
 
-    def autotune(self, sid: int, r, precision=PREC_DF32) -> int:
-        """Pick the wave size by timing a band of this render; returns paths per wave."""
+    def autotune(self, sid: int, r, precision=PREC_DF32) -> dict:
+        """Pick the trace launch shape (wave size, lanes, grid sizes) by timing a band of this
+        render; returns the choice (kept for the scene's size class)."""
         d = render_desc(r, precision)
-        n = C.c_int32()
-        _check(self.lib.hpt_autotune(self.h, C.c_uint64(sid), C.byref(d), C.byref(n)))
-        return n.value
+        t = Tuning()
+        _check(self.lib.hpt_autotune(self.h, C.c_uint64(sid), C.byref(d), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def sync(self):
         _check(self.lib.hpt_sync(self.h))

@@ -433,6 +433,45 @@ def config3_render(**kw) -> Render:
 
 
 # ---------------------------------------------------------------------------
+# config 4: the serving stream
+# ---------------------------------------------------------------------------
+SCENE_MEDIAN_DEPTH = {"cfg0": 7.5 * MM, "cfg1": 17.5 * MM, "cfg3": 17.5 * MM}
+CONFIG4_SLM_SIZES = ((512, 512), (1920, 1080), (3840, 2160))
+CONFIG4_SPP = (16, 32, 64, 128, 256)
+CONFIG4_K = (1, 4, 8)
+
+
+def pose_T(dx, dy, dz):
+    """Rigid world -> hologram transform of an eye offset (dx, dy) and an axial shift dz."""
+    T = np.eye(4)
+    T[0, 3], T[1, 3], T[2, 3] = -dx, -dy, -dz
+    return T
+
+
+def config4_requests(n, seed=4242):
+    """n render requests of the serving stream: a workload drawn uniformly from configs 0-3 (its
+    scene and its own pitch, wavelengths, depth and cache use; configs 1 and 2 share the scene),
+    an SLM size drawn from 512x512, 1920x1080 and 3840x2160, spp from {16, ..., 256}, K from
+    {1, 4, 8}, an eye offset U[-5, 5] mm in x and y and a focal depth U[5, 30] mm (the axial shift
+    that puts the scene's median depth there).  Returns [(scene key, Render)]: the keys are
+    "cfg0", "cfg1" and "cfg3".  Arrival times are drawn by the caller."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        cfg = int(rng.integers(0, 4))
+        W, H = CONFIG4_SLM_SIZES[int(rng.integers(0, 3))]
+        spp = int(rng.choice(CONFIG4_SPP))
+        K = int(rng.choice(CONFIG4_K))
+        dx, dy = rng.uniform(-5 * MM, 5 * MM, 2)
+        df = rng.uniform(5 * MM, 30 * MM)
+        key = "cfg0" if cfg == 0 else ("cfg1" if cfg in (1, 2) else "cfg3")
+        T = pose_T(dx, dy, SCENE_MEDIAN_DEPTH[key] - df)
+        make = {0: config0_render, 1: config1_render, 2: config2_render, 3: config3_render}[cfg]
+        out.append((key, make(W=W, H=H, spp=spp, K=K, T=T, seed=100 + k)))
+    return out
+
+
+# ---------------------------------------------------------------------------
 # small scenes used by tests
 # ---------------------------------------------------------------------------
 def emissive_plane_scene(z=5 * MM, half=3 * MM, Le=1.0) -> Scene:

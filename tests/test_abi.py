@@ -50,6 +50,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(hpt_bake_desc), offsetof(hpt_bake_desc, spp), offsetof(hpt_bake_desc, seed));
   printf("%zu\n", offsetof(hpt_render_desc, omit_obliquity));
   printf("%zu\n", offsetof(hpt_ctx_desc, max_queue));
+  printf("%zu %zu %zu %d %d\n", sizeof(hpt_tuning), offsetof(hpt_tuning, band_ms), offsetof(hpt_tuning, band_path_samples),
+         HPT_ERR_CANCELLED, HPT_CTX_FAIL_SERVING_WAVES);
   return 0;
 }
 '''
@@ -67,7 +69,9 @@ int main(void) {
            hpt.KERNEL_NAMES.index("k_trace"), hpt.KERNEL_NAMES.index("k_accum"),
            hpt.RenderDesc.grf_phi.offset, hpt.RenderDesc.grf_nx.offset, hpt.RenderDesc.grf_ny.offset, S_PHASE_GRF,
            C.sizeof(hpt.BakeDesc), hpt.BakeDesc.spp.offset, hpt.BakeDesc.seed.offset,
-           hpt.RenderDesc.omit_obliquity.offset, hpt.CtxDesc.max_queue.offset]
+           hpt.RenderDesc.omit_obliquity.offset, hpt.CtxDesc.max_queue.offset,
+           C.sizeof(hpt.Tuning), hpt.Tuning.band_ms.offset, hpt.Tuning.band_path_samples.offset,
+           [k for k, v in hpt.STATUS_NAMES.items() if v == "CANCELLED"][0], hpt.CTX_FAIL_SERVING_WAVES]
     assert [int(x) for x in out] == got
 
 

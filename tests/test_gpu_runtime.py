@@ -71,10 +71,16 @@ def test_autotune_keeps_results(torch_cuda):
         r = S.config1_render(W=320, H=180, spp=8, K=2)
         out = hpt.alloc_output(r)
         before = _trace(ctx, sid, r, out)
-        n = ctx.autotune(sid, S.config2_render())
-        assert n in (1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24)
-        after = _trace(ctx, sid, r, out)
+        t = ctx.autotune(sid, S.config2_render())
+        assert t["paths_per_wave"] in (1 << 21, 1 << 22, 1 << 23, 1 << 24)
+        assert 1 <= t["lanes"] <= 4 and t["trace_blocks_per_sm"] >= 1 and t["shade_blocks_per_sm"] >= 1
+        assert t["scene_class"] == 1 and t["candidates"] >= 4
+        assert 0 < t["band_ms"] <= t["band_ms_start"] and t["band_path_samples"] >= 50_000_000
+        after = _trace(ctx, sid, r, out)      # traced with the tuned shape of the scene's class
         assert np.array_equal(before, after)
+        host = np.empty(after.shape, np.complex64)
+        ctx.trace_host(sid, r, host)
+        assert np.array_equal(host, before)
     finally:
         ctx.close()
 

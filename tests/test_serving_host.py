@@ -1,5 +1,6 @@
-"""Host logic of the serving measurement (no GPU): Poisson submission, BUSY answers counted as
-rejections, latency and rate statistics from the request timestamps."""
+"""Host logic of the serving measurement (no GPU): Poisson submission with library-owned outputs,
+BUSY answers counted as rejections, every completed request released once, latency and rate
+statistics from the request timestamps."""
 import os
 import sys
 import types
@@ -21,20 +22,28 @@ class _FakeCtx:
     an admission delay of 2 ms."""
 
     def __init__(self, fail_status=-5):
-        self.n, self.accepted, self.fail_status = 0, [], fail_status
+        self.n, self.accepted, self.fail_status, self.released = 0, [], fail_status, []
 
     def sync(self):
         pass
 
     def submit(self, sid, r, out, precision=1):
+        assert out is None                      # outputs owned by the library
         self.n += 1
         if self.n % 3 == 0:
             raise _Err(self.fail_status)
         self.accepted.append(self.n)
         return self.n
 
+    def poll(self, i):
+        return i % 2 == 0                       # even ids finish early, odd ones need a wait
+
     def wait(self, i, timeout_ms):
         pass
+
+    def request_release(self, i):
+        assert i not in self.released
+        self.released.append(i)
 
     def request_times(self, i):
         t0 = 10e3 * i
@@ -42,8 +51,8 @@ class _FakeCtx:
 
 
 def _requests(n):
-    r = types.SimpleNamespace(K=4, path_samples=lambda: 1000)
-    return [(1, r, 1, None) for _ in range(n)]
+    r = types.SimpleNamespace(K=4, W=64, H=32, path_samples=lambda: 1000)
+    return [(1, r) for _ in range(n)]
 
 
 @pytest.fixture(scope="module")
@@ -54,29 +63,31 @@ def bench():
 
 
 def test_busy_answers_are_counted_and_excluded(bench):
-    hpt = types.SimpleNamespace(HptError=_Err)
     ctx = _FakeCtx()
-    res = bench.serve(ctx, hpt, None, _requests(9), 1e6, 0)
-    assert res["requests"] == 9 and res["rejected"] == 3
+    res = bench.serve_owned(ctx, types.SimpleNamespace(HptError=_Err, PREC_DF32=1), _requests(9), 1e6, 0)
+    assert res["requests"] == 9 and res["rejected"] == 3 and res["completed"] == 6
+    assert sorted(ctx.released) == ctx.accepted
     ids = ctx.accepted                                   # 1, 2, 4, 5, 7, 8
     span = (10e3 * ids[-1] + 50e3 - 10e3 * ids[0]) / 1e6
     assert res["completed_rate_per_s"] == pytest.approx(6 / span)
     assert res["p50_latency_s"] == pytest.approx(0.05) and res["p99_latency_s"] == pytest.approx(0.05)
-    assert res["mean_queue_s"] == pytest.approx(0.002) and res["p99_queue_s"] == pytest.approx(0.002)
+    assert res["p50_queue_s"] == pytest.approx(0.002) and res["p99_queue_s"] == pytest.approx(0.002)
+    assert res["latency_by_slm"] == {"64x32": {"completed": 6, "p50_latency_s": pytest.approx(0.05),
+                                                "p99_latency_s": pytest.approx(0.05)}}
     assert res["holograms_per_s"] == pytest.approx(6 * 4 / span)
     assert res["path_samples_per_s"] == pytest.approx(6 * 1000 / span)
 
 
 def test_other_errors_are_not_swallowed(bench):
-    hpt = types.SimpleNamespace(HptError=_Err)
+    hpt = types.SimpleNamespace(HptError=_Err, PREC_DF32=1)
     with pytest.raises(_Err):
-        bench.serve(_FakeCtx(fail_status=-1), hpt, None, _requests(4), 1e6, 0)
+        bench.serve_owned(_FakeCtx(fail_status=-1), hpt, _requests(4), 1e6, 0)
 
 
 def test_all_rejected_gives_counts_only(bench):
     class AllBusy(_FakeCtx):
         def submit(self, *a, **k):
             raise _Err(-5)
-    hpt = types.SimpleNamespace(HptError=_Err)
-    res = bench.serve(AllBusy(), hpt, None, _requests(3), 1e6, 0)
+    hpt = types.SimpleNamespace(HptError=_Err, PREC_DF32=1)
+    res = bench.serve_owned(AllBusy(), hpt, _requests(3), 1e6, 0)
     assert res == {"requests": 3, "rejected": 3, "offered_rate_per_s": 1e6}
