@@ -205,12 +205,16 @@ def cpu_oracle_rate(scene, r, n_pixels, seed=5):
     return samples / dt, dt, cores, samples, pix, U
 
 
-def precision_report(U, ref):
+def precision_report(U, ref, flags_of=None):
     """Error of GPU fields U[lambda][m][pixel] against the FP64 oracle's ref, per output: the
     fraction of pixels within 1e-4 relative error and 1e-3 rad (where |ref| < 1e-3 RMS the bound
     is 1e-4 RMS; the phase is checked where |ref| >= 0.1 RMS), the median and maximum relative
-    error and the maximum phase error."""
-    out = []
+    error and the maximum phase error.  flags_of(pixel indices) -> (flags, sens) of the oracle
+    for those pixels: the pixels out of the bar are then counted by what the oracle flags in
+    them (an edge or tie hit, an ill-conditioned incoherent part, an incoherent path through a
+    mirror or dielectric, or a field that float32-sized moves of the image points change by the
+    tolerance), and the ones it does not flag are counted as unattributed."""
+    out, fails = [], []
     for l in range(U.shape[0]):
         for m in range(U.shape[1]):
             u, q = np.asarray(U[l, m], np.complex128), np.asarray(ref[l, m], np.complex128)
@@ -221,8 +225,25 @@ def precision_report(U, ref):
             ok = (rel <= 1e-4) & (ph <= 1e-3)
             out.append({"lambda": l, "m": m, "pass_frac": float(ok.mean()), "median_rel": float(np.median(rel)),
                         "max_rel": float(rel.max()), "max_phase_rad": float(ph.max())})
-    return {"outputs": out, "min_pass_frac": min(x["pass_frac"] for x in out),
-            "max_phase_rad": max(x["max_phase_rad"] for x in out), "pixels": int(U.shape[2])}
+            tol = 1e-4 * np.maximum(a, 1e-3 * rms)
+            fails += [(l, int(i), float(tol[i])) for i in np.nonzero(~ok)[0]]
+    rep = {"outputs": out, "min_pass_frac": min(x["pass_frac"] for x in out),
+           "max_phase_rad": max(x["max_phase_rad"] for x in out), "pixels": int(U.shape[2]),
+           "failing_pixel_outputs": len(fails)}
+    if flags_of is not None and fails:
+        pix = sorted({i for _, i, _ in fails})
+        fl, sens = flags_of(np.asarray(pix))
+        col = {p: k for k, p in enumerate(pix)}
+        cats = {"near_edge": 0, "ill_conditioned": 0, "incoherent_delta": 0, "sensitive_only": 0, "unattributed": 0}
+        for l, i, tol in fails:
+            f, sv = int(fl[l, col[i]]), float(sens[l, col[i]])
+            if f & 0xFFFF: cats["near_edge"] += 1
+            elif (f >> 16) & 0xFFFF: cats["ill_conditioned"] += 1
+            elif (f >> 32) & 0xFFFF: cats["incoherent_delta"] += 1
+            elif sv >= tol: cats["sensitive_only"] += 1
+            else: cats["unattributed"] += 1
+        rep["failing_by_oracle_flag"] = cats
+    return rep
 
 
 def run_optics(ctx, hpt, torch, r, out, sid, stream, reps=3):
@@ -597,15 +618,24 @@ def main():
         rate, dt, cores, nsamp, pix, ref = cpu_oracle_rate(sc, r, npx)
         pix_t = torch.from_numpy(np.asarray(pix)).to(out.device)
         U_df = out.reshape(out.shape[0], out.shape[1], -1)[:, :, pix_t].cpu().numpy()
-        precision = {"df32": precision_report(U_df, ref)}
+        import oracle
+        orc = oracle.Oracle(sc)
+        pix_np = np.asarray(pix)
+
+        def flags_df(sel):
+            _, fl, sv = orc.trace(r, pix_np[sel], with_flags=True)
+            return fl, sv
+        precision = {"df32": precision_report(U_df, ref, flags_df)}
         if not args.no_plain:
             # the plain form renders each wavelength on its own (wavelength index 0 in the draws):
             # its reference is the oracle on those single-wavelength renders
-            import oracle
-            orc = oracle.Oracle(sc)
             U_64 = np.stack([o.reshape(o.shape[1], -1)[:, pix_t].cpu().numpy() for o in outs_plain])
-            ref_64 = np.concatenate([orc.trace(rp, np.asarray(pix)) for rp in r_plain])
-            precision["fp64"] = precision_report(U_64, ref_64)
+            ref_64 = np.concatenate([orc.trace(rp, pix_np) for rp in r_plain])
+
+            def flags_64(sel):
+                res = [orc.trace(rp, pix_np[sel], with_flags=True) for rp in r_plain]
+                return np.concatenate([x[1] for x in res]), np.concatenate([x[2] for x in res])
+            precision["fp64"] = precision_report(U_64, ref_64, flags_64)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{npx} seeded random pixels of the {r.W}x{r.H} frame x {len(r.lambdas)} wavelengths x "
                          f"{r.spp} spp ({nsamp} path samples, {dt:.1f} s)"}

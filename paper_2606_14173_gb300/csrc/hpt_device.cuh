@@ -17,7 +17,8 @@ namespace hpt {
 #define SHADOW_SHRINK 1e-5f
 #define NEAR_MARGIN 1e-4f       // barycentric band treated as "near an edge" on coherent rays
 #define TIE_REL 2e-6f           // relative distance band treated as a tie on coherent rays
-#define WATERTIGHT_EPS 2e-5f    // barycentric slack of float tests on incoherent rays
+#define WATERTIGHT_EPS 2e-5f    // most barycentric slack of float tests on incoherent rays (per
+                                // triangle: a band of 1e-6 x the scene's largest coordinate)
 #define PI_F 3.14159265358979f
 #define INV_PI_F 0.318309886183791f
 
@@ -33,6 +34,13 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b)
     return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+// the same products with every rounding spelled out (fixed FMA contraction), so that a result does
+// not depend on how the compiler contracts the surrounding code of a given build
+__device__ __forceinline__ float dot3_rn(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, __fmul_rn(a.z, b.z))); }
+__device__ __forceinline__ float3 cross3_rn(float3 a, float3 b)
+{
+    return f3(fmaf(a.y, b.z, -__fmul_rn(a.z, b.y)), fmaf(a.z, b.x, -__fmul_rn(a.x, b.z)), fmaf(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
 __device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
 
 template <class R> struct R3 {
@@ -103,13 +111,16 @@ struct Counters {
     unsigned rays, boxes, tris, refines, fallbacks, shadows, bounces, samples;
 };
 
+
 // Closest (or any) hit of a float ray against the BVH.  TRACK: collect the triangles met within
 // NEAR_MARGIN of an edge, or tied in distance within TIE_REL, no farther than the float winner,
-// so that the caller can re-decide the hit in the coherent arithmetic.
+// so that the caller can re-decide the hit in the coherent arithmetic.  The traversal stack has
+// slimit entries (stride SSTRIDE); a deeper tree sets ST_STACK_OVERFLOW.
+
 template <bool STATS, int SSTRIDE>
 __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d, float tmax, int skip, float eps_w,
-                                         bool TRACK, bool ANYHIT, HitF &h, Cands &cand, int *stk, int &status,
-                                         Counters &cnt)
+                                         bool TRACK, bool ANYHIT, HitF &h, Cands &cand, int *stk, int slimit,
+                                         int &status, Counters &cnt)
 {
     const float big = 1e30f;
     float3 inv = f3(fabsf(d.x) > 1e-20f ? 1.0f / d.x : copysignf(1e20f, d.x),
@@ -135,22 +146,22 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     int LEAF = 0;                   // pending leaf (< 0); 0 = none (the root is never a leaf)
     for (;;) {
         while (node >= 0 && node != SENT) {
+            float tl = h.t * cull;
             const float4 *np = nodes + 4 * node;
             float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
-            float tl = h.t * cull;
             float a0 = n0.x * inv.x - ood.x, b0 = n0.y * inv.x - ood.x;
             float a1 = n0.z * inv.y - ood.y, b1 = n0.w * inv.y - ood.y;
             float a2 = n2.x * inv.z - ood.z, b2 = n2.y * inv.z - ood.z;
-            float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
-            float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tl));
             float e0 = n1.x * inv.x - ood.x, f0 = n1.y * inv.x - ood.x;
             float e1 = n1.z * inv.y - ood.y, f1 = n1.w * inv.y - ood.y;
             float e2 = n2.z * inv.z - ood.z, f2 = n2.w * inv.z - ood.z;
+            int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
+            float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tl));
             float c1min = fmaxf(fmaxf(fminf(e0, f0), fminf(e1, f1)), fmaxf(fminf(e2, f2), 0.0f));
             float c1max = fminf(fminf(fmaxf(e0, f0), fmaxf(e1, f1)), fminf(fmaxf(e2, f2), tl));
             if (STATS) cnt.boxes += 2;
             bool h0 = c0min <= c0max, h1 = c1min <= c1max;
-            int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
             if (!h0 && !h1) {
                 node = sp > 0 ? stk[(--sp) * SSTRIDE] : SENT;
             } else {
@@ -158,7 +169,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
                 if (h0 && h1) {
                     int other = l1;
                     if (c1min < c0min) { node = l1; other = l0; }
-                    if (sp < TSTACK) stk[(sp++) * SSTRIDE] = other;
+                    if (sp < slimit) stk[(sp++) * SSTRIDE] = other;
                     else status |= ST_STACK_OVERFLOW;
                 }
             }
@@ -179,19 +190,23 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
                 if (STATS) cnt.tris++;
                 if (id == skip) continue;
                 float3 e1 = xyz(E1), e2 = xyz(E2);
-                float3 pv = cross3(d, e2);
-                float det = dot3(e1, pv);
+                float3 pv = cross3_rn(d, e2);
+                float det = dot3_rn(e1, pv);
                 float idet = __fdividef(1.0f, det);
                 float3 tv = o - xyz(A);
-                float u = dot3(tv, pv) * idet;
-                float3 qv = cross3(tv, e1);
-                float v = dot3(d, qv) * idet;
-                float t = dot3(e2, qv) * idet;
+                float u = __fmul_rn(dot3_rn(tv, pv), idet);
+                float3 qv = cross3_rn(tv, e1);
+                float v = __fmul_rn(dot3_rn(d, qv), idet);
+                float t = __fmul_rn(dot3_rn(e2, qv), idet);
                 if (TRACK) {
                     const float m = fminf(fminf(u, v), 1.0f - u - v);
                     if (fabsf(m) < NEAR_MARGIN && t > 0.0f && t <= h.t * (1.0f + 10.0f * TIE_REL)) cand.add(t, id);
                 }
-                bool inside = (u >= -eps_w) && (v >= -eps_w) && (u + v <= 1.0f + eps_w) && (t > 0.0f);
+                // the slack of a float test closes cracks between neighbours; per triangle it is a
+                // band of fixed width in space (E1.w), so that large triangles do not grow far
+                // past their outer edges
+                const float ew = eps_w > 0.0f ? E1.w : 0.0f;
+                bool inside = (u >= -ew) && (v >= -ew) && (u + v <= 1.0f + ew) && (t > 0.0f);
                 if (!inside) continue;
                 if (ANYHIT) {
                     if (t < tmax) { h.t = t; h.tri = id; return true; }
@@ -221,7 +236,8 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
 // ties to the lower triangle id -- the decision rule of the definition.
 template <int SSTRIDE>
 __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double oy, double oz, double dx, double dy,
-                                          double dz, double tmin, int skip, double *t_out, int *stk, int &status)
+                                          double dz, double tmin, int skip, double *t_out, int *stk, int slimit,
+                                          int &status)
 {
     double ix = fabs(dx) > 1e-300 ? 1.0 / dx : 1e300, iy = fabs(dy) > 1e-300 ? 1.0 / dy : 1e300,
            iz = fabs(dz) > 1e-300 ? 1.0 / dz : 1e300;
@@ -234,6 +250,7 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
             float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
             double lo0[3] = {n0.x, n0.z, n2.x}, hi0[3] = {n0.y, n0.w, n2.y};
             double lo1[3] = {n1.x, n1.z, n2.z}, hi1[3] = {n1.y, n1.w, n2.w};
+            const int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
             double o[3] = {ox, oy, oz}, iv[3] = {ix, iy, iz};
             double t0a = 0.0, t0b = best * (1.0 + 1e-9), t1a = 0.0, t1b = best * (1.0 + 1e-9);
             for (int k = 0; k < 3; ++k) {
@@ -243,7 +260,6 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
                 t1a = fmax(t1a, fmin(a, b)); t1b = fmin(t1b, fmax(a, b));
             }
             bool h0 = t0a <= t0b, h1 = t1a <= t1b;
-            int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
             if (!h0 && !h1) {
                 if (sp == 0) { *t_out = best; return best_id; }
                 node = stk[(--sp) * SSTRIDE];
@@ -252,7 +268,7 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
                 if (h0 && h1) {
                     int other = l1;
                     if (t1a < t0a) { node = l1; other = l0; }
-                    if (sp < TSTACK) stk[(sp++) * SSTRIDE] = other;
+                    if (sp < slimit) stk[(sp++) * SSTRIDE] = other;
                     else status |= ST_FALLBACK_STACK;
                 }
             }

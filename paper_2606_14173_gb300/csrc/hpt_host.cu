@@ -629,8 +629,20 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
                     *p2 = d->verts + 3 * d->tris[3 * t + 2];
         float idf;
         memcpy(&idf, &t, 4);
+        // barycentric slack of the float test on incoherent rays: a band of 1e-6 x the scene's
+        // largest coordinate (a few float ulps of a hit point) across the triangle's shortest
+        // altitude, at most 2e-5
+        double a[3] = {(double)p1[0] - p0[0], (double)p1[1] - p0[1], (double)p1[2] - p0[2]};
+        double b[3] = {(double)p2[0] - p0[0], (double)p2[1] - p0[1], (double)p2[2] - p0[2]};
+        double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        double area2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        double c3[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double lmax = sqrt(std::max({a[0] * a[0] + a[1] * a[1] + a[2] * a[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2],
+                                     c3[0] * c3[0] + c3[1] * c3[1] + c3[2] * c3[2]}));
+        double hmin = lmax > 0.0 ? area2 / lmax : 0.0;
+        float slack = hmin > 0.0 ? (float)std::min(2e-5, 1e-6 * (double)max_abs / hmin) : 2e-5f;
         tri4[3 * i] = make_float4(p0[0], p0[1], p0[2], idf);
-        tri4[3 * i + 1] = make_float4(p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2], 0.0f);
+        tri4[3 * i + 1] = make_float4(p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2], slack);
         tri4[3 * i + 2] = make_float4(p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2], 0.0f);
     }
     std::vector<double> ref64((size_t)nt * REF_N, 0.0);
@@ -753,6 +765,7 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     s.cache_res = d->cache_res;
     s.n_tris = nt;
     s.n_nodes = n_knodes;
+    s.bvh_depth = B.max_depth_seen;
     s.n_lights = d->nl;
     s.n_points = d->np;
     rec->n_nodes = n_knodes;
@@ -1073,6 +1086,7 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
             g.path_offset = wd.n_paths;
             wd.n_paths += take * spp;
             wd.n_items += take;
+            wd.stack_n = std::max(wd.stack_n, stack_entries(jobs[j].sc.bvh_depth));
             max_depth = std::max(max_depth, jobs[j].max_depth);
             c += take;
         }
@@ -1343,8 +1357,8 @@ extern "C" hpt_status hpt_trace_timed(hpt_ctx *ctx, uint64_t scene_id, const hpt
     cudaError_t e = cudaStreamSynchronize(ctx->wstream);
     for (int k = 0; k < HPT_NKERNELS; ++k) kernel_ms[k] = 0.0f, launches[k] = 0;
     if (!st && e == cudaSuccess) {
-        // shade launches the coherent and the incoherent kernel back to back
-        static const uint32_t per_call[HPT_NKERNELS] = {1, 1, 2, 1};
+        // trace and shade each launch a coherent and an incoherent kernel back to back
+        static const uint32_t per_call[HPT_NKERNELS] = {1, 2, 2, 1};
         for (size_t i = 0; i + 1 < tm.used && e == cudaSuccess; ++i) {
             const int k = tm.kind[i];
             if (k < 0) continue;
@@ -1841,6 +1855,7 @@ static void sched_loop(hpt_ctx *ctx)
                         g.path_offset = wd.n_paths;
                         wd.n_paths += pk.second * r.job.spp;
                         wd.n_items += pk.second;
+                        wd.stack_n = std::max(wd.stack_n, stack_entries(r.job.sc.bvh_depth));
                         max_depth = std::max(max_depth, r.job.max_depth);
                     }
                     // this wave's lane: path state, scratch and stream of its own

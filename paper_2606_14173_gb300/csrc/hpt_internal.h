@@ -13,7 +13,7 @@ constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
 #ifndef HPT_TSTACK
 #define HPT_TSTACK 32
 #endif
-constexpr int TSTACK = HPT_TSTACK; // traversal stack entries per thread (shared memory)
+constexpr int TSTACK = HPT_TSTACK; // most traversal stack entries per thread (shared memory)
 constexpr int TRACE_BLOCK = 128;   // threads per block of the trace kernel
 constexpr int SHADE_BLOCK = 128;
 constexpr int GEN_BLOCK = 256;
@@ -54,6 +54,7 @@ constexpr int REF_N = 10;   // n.xyz, d0, m1.xyz, m2.xyz
 
 struct DevScene {
     const float4 *nodes;      // 4 float4 per BVH2 node (child boxes + child links)
+    int bvh_depth;            // inner levels above the deepest leaf: traversal stack entries needed
     const float4 *tri4;       // 3 float4 per triangle in leaf order: (v0, id), e1, e2
     const double *ref64;      // [nt][REF_N]
     const float2 *refdf;      // [nt][REF_N] (hi, lo)
@@ -124,7 +125,7 @@ struct WaveDesc {
     int n_seg;
     int n_paths;
     int n_items;
-    int pad;
+    int stack_n;      // traversal stack entries per thread of the trace kernels (<= TSTACK)
     WaveSeg seg[MAX_SEG];
 };
 
@@ -147,6 +148,10 @@ struct PathBufs {
     int *q[3][2];                        // queues (coherent, incoherent, shadow) x ping-pong
     int capacity;
 };
+
+// traversal stack entries per thread for a BVH of the given depth (inner levels above the
+// deepest leaf): a near-first traversal holds at most one entry per level; one spare
+inline int stack_entries(int bvh_depth) { return bvh_depth + 1 < 2 ? 2 : (bvh_depth + 1 > TSTACK ? TSTACK : bvh_depth + 1); }
 
 // device-side scratch of one launch slot
 struct SlotScratch {

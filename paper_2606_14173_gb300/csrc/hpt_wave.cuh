@@ -238,27 +238,35 @@ __device__ __forceinline__ bool exact_hit(const DevScene &sc, int tri, const R3<
 #ifndef HPT_TRACE_MINB
 #define HPT_TRACE_MINB 8
 #endif
+#ifndef HPT_TRACE_INC_MINB
+#define HPT_TRACE_INC_MINB 8        // the incoherent / shadow-ray trace kernel
+#endif
 #ifndef HPT_ACCUM_MINB
 #define HPT_ACCUM_MINB 1
 #endif
 
-template <class R, bool STATS>
-__global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
-                                                       SlotScratch *__restrict__ scr, int it)
+// COH = true: the coherent queue of the iteration (closest hit with the re-decision of uncertain
+// hits in the coherent arithmetic); false: the incoherent and shadow queues (float closest / any
+// hit only), so that the second kernel carries none of the coherent code and its registers.
+template <class R, bool STATS, bool COH>
+__global__ void __launch_bounds__(TRACE_BLOCK, COH ? HPT_TRACE_MINB : HPT_TRACE_INC_MINB)
+    k_trace(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb, SlotScratch *__restrict__ scr, int it)
 {
     using RO = RealOps<R>;
-    __shared__ int s_stack[TSTACK * TRACE_BLOCK];
+    extern __shared__ int s_stack[];          // wd.stack_n traversal stack entries per thread
     int *stk = s_stack + threadIdx.x;
-    const int nc = scr->qcount[it][0], ni = scr->qcount[it][1], ns = scr->qcount[it][2];
+    const int slimit = wd.stack_n;
+    const int nc = COH ? scr->qcount[it][0] : 0;
+    const int ni = COH ? 0 : scr->qcount[it][1], ns = COH ? 0 : scr->qcount[it][2];
     const int total = nc + ni + ns;
     const int par = it & 1;
     int status = 0;
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int idx = blockIdx.x * TRACE_BLOCK + threadIdx.x; idx < total; idx += gridDim.x * TRACE_BLOCK) {
         int kind, qi;
-        if (idx < nc) { kind = 0; qi = idx; }
-        else if (idx < nc + ni) { kind = 1; qi = idx - nc; }
-        else { kind = 2; qi = idx - nc - ni; }
+        if (COH) { kind = 0; qi = idx; }
+        else if (idx < ni) { kind = 1; qi = idx; }
+        else { kind = 2; qi = idx - ni; }
         const int e = pb.q[kind][par][qi];
         if (kind < 2 && (e & Q_FINALIZE)) continue;   // no ray: a path that only waits for its shadow ray, or none
         const int p = e;
@@ -272,15 +280,16 @@ __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const Job
             if (STATS) cnt.shadows++;
             const float4 s4 = pb.sh_d[p];
             const bool any = traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(s4), s4.w, skip, WATERTIGHT_EPS, false, true, h,
-                                                          cand, stk, status, cnt);
+                                                          cand, stk, slimit, status, cnt);
             pb.occl[p] = any ? 1 : 0;
         } else if (kind == 1) {
             if (STATS) cnt.bounces++;
             traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, WATERTIGHT_EPS, false, false, h, cand, stk,
-                                         status, cnt);
+                                         slimit, status, cnt);
             pb.hit[p] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
-        } else {
-            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, 0.0f, true, false, h, cand, stk, status, cnt);
+        } else if constexpr (COH) {
+            traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, 0.0f, true, false, h, cand, stk, slimit,
+                                         status, cnt);
             int tri = h.tri;
             if (cand.n > 0) {
                 // the float test was within its error band: decide among the candidates (and the
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, HPT_TRACE_MINB) k_trace(const Job
                     double tt;
                     tri = traverse_fp64<TRACE_BLOCK>(sc, RO::to_d(co.x), RO::to_d(co.y), RO::to_d(co.z), RO::to_d(cd.x),
                                                      RO::to_d(cd.y), RO::to_d(cd.z), cont ? COH_TMIN : 0.0, skip,
-                                                     &tt, stk, status);
+                                                     &tt, stk, slimit, status);
                 }
             }
             pb.hit[p] = make_float4(h.t, 0.0f, 0.0f, __int_as_float(tri));
@@ -727,7 +736,7 @@ __device__ __noinline__ float2 point_field(const DevJob *Jp, int lam, int px, in
         Cands cand;
         Counters dummy;
         if (traverse<false, ACCUM_BLOCK>(sc, Of, dw * (1.0f / dist), dist * (1.0f - SHADOW_SHRINK), -1, WATERTIGHT_EPS,
-                                         false, true, h, cand, stk, status, dummy))
+                                         false, true, h, cand, stk, TSTACK, status, dummy))
             continue;
         const float turns = RO::frac_f(r * RO::rc(J.inv_lambda[lam]));
         float sn, cs;

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2606_14173_gb300 import scenes as S
-from tests.parity import assert_parity, assert_parity_explained, compare
+from tests.parity import assert_parity, assert_parity_explained, attribute, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -86,9 +86,18 @@ def test_headline_config_full_size_sampled(ctx, cfg1, prec):
     rng = np.random.default_rng(11)
     tile = (np.arange(900, 964)[:, None] * r.W + np.arange(1000, 1064)[None, :]).reshape(-1)
     pix = np.concatenate([tile, rng.choice(r.W * r.H, 1024, replace=False)])
-    ref = orc.trace(r, pix)
+    ref, flags, sens = orc.trace(r, pix, with_flags=True)
     got = U.reshape(3, 8, -1)[:, :, pix]
     assert_parity(got, ref, f"cfg2 sampled prec={prec}")
+    # every pixel out of the bar is one the oracle flags: an edge or tie hit, or an incoherent
+    # part that float32-sized moves of the image point change by at least the tolerance
+    reps = attribute(got, ref, flags, sens)
+    failing = sum(x["failing"] for x in reps)
+    assert all(x["attributed"] == x["failing"] for x in reps), [(x["failing"], x["attributed"]) for x in reps]
+    print(f"cfg2 prec={prec}: {failing} of {sum(x['n'] for x in reps)} pixel outputs out of the bar, all flagged "
+          f"(near edge {sum(x['failing_near_edge'] for x in reps)}, ill-conditioned "
+          f"{sum(x['failing_ill_conditioned'] for x in reps)}, incoherent delta "
+          f"{sum(x['failing_incoherent_delta'] for x in reps)})")
 
 
 def test_precisions_agree(ctx, cfg1):

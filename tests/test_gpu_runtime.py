@@ -128,8 +128,9 @@ def test_timed_trace_reports_kernels_and_keeps_results(torch_cuda):
         assert set(t) == set(hpt.KERNEL_NAMES)
         waves = t["k_gen"][1]
         assert waves >= 1 and t["k_accum"][1] == waves
-        assert t["k_trace"][1] == waves * (r.max_depth + 1)
-        assert t["k_shade"][1] == 2 * t["k_trace"][1]
+        # per iteration one coherent-ray and one incoherent/shadow-ray kernel of each kind
+        assert t["k_trace"][1] == 2 * waves * (r.max_depth + 1)
+        assert t["k_shade"][1] == t["k_trace"][1]
         assert all(ms > 0 for ms, _ in t.values())
     finally:
         ctx.close()
