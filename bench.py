@@ -46,11 +46,12 @@ ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 # 30 per float ray-triangle test, 400 per coherent re-decision in double-float, 120 per
 # incoherent vertex (shadow ray or BSDF bounce), 25 per hologram of a path sample (phase + Kahan sum)
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
-# DRAM bytes (read + write) per k_trace launch, averaged over every k_trace launch of one frame of
-# the 1920x270 band of the 30-sphere scene (same wave size as the full 1080p frame) in one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), copied here: the bench cannot read
-# hardware counters itself.  None whenever k_trace changed since that capture.
-TRACE_DRAM_BYTES_PER_LAUNCH = 401.2e6
+# DRAM bytes (read + write) per k_trace launch: the average over every launch of both trace
+# kernels in one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 1920x270 band
+# of the 30-sphere scene with 2,097,152-path waves, scaled by 4.0 to the 8,388,608-path waves of
+# the headline frame (the traffic is per ray), copied here: the bench cannot read hardware
+# counters itself.  None whenever k_trace changed since that capture.
+TRACE_DRAM_BYTES_PER_LAUNCH = 138e6
 
 
 # name -> (description, scene factory, render factory)
@@ -580,8 +581,8 @@ def main():
     probes = ctx.probe_peaks() if not args.no_counters else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": ("copied from one ncu capture of k_trace on the 1920x270 band (same wave size)"
-                                   if traffic is not None else None),
+                "traffic_source": ("ncu capture of both trace kernels on the 1920x270 band with 2M-path waves, "
+                                   "scaled x4.0 to the 8M-path waves of this frame" if traffic is not None else None),
                 "kernel": "k_trace",
                 "measured_probes": probes,
                 "frac_of_measured_fp32": (achieved / probes["fp32_tflops"]) if probes else None,
