@@ -255,7 +255,7 @@ hpt_status hpt_autotune(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *
  * nx^2 ny^2), xi_m = 2 pi u24(Philox4x32-10(kx mod nx, ky mod ny, m, 0x47524600; phase_seed)),
  * and writes phi_m = arg r_m in radians, float [K][ny][nx], to phi_dev (caller-owned device
  * memory, 4 K nx ny bytes).  nx, ny: powers of two, 2 .. 8192.  Runs on 'stream' (NULL: the
- * legacy default stream); its scratch (16 nx ny bytes and the twiddle tables) comes from the
+ * legacy default stream); its scratch (8 nx ny bytes and the twiddle tables) comes from the
  * device's stream-ordered pool and is released on the stream.  The paper's own numbers for the
  * grid are not given: the caller chooses it to cover the image points' hologram positions
  * (the field is periodic). */
@@ -271,8 +271,9 @@ hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t hologram_off
  * imaginary), transformed back and cropped to the original window.  lambdas: host array of
  * n_lambda wavelengths (m).  Wp, Hp <= 8192.  Asynchronous on 'stream'.  The zero padding is
  * never stored: the scratch, from the device's stream-ordered pool and released on the
- * stream, is 8 (2 max(Wp Hp, min(K, 8) Wp H) + n_lambda Wp Hp) bytes (the K fields of a
- * wavelength go through in groups of up to 8). */
+ * stream, is 8 (min(K, 8) Wp H + n_lambda Wp Hp + Wp + Hp) bytes (the K fields of a
+ * wavelength go through in groups of up to 8; their spectra stay row-major, the column
+ * transforms read and write them in place). */
 hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *out_dev, int32_t W, int32_t H,
                              int32_t n_lambda, int32_t K, const double *lambdas, double pitch, double z,
                              void *stream);

@@ -126,10 +126,10 @@ __host__ __device__ constexpr int fft_ns(int logn, int p) { return p == 0 ? 1 : 
 // x[j + r N/R] (r < R) through 'ld', multiplies it by exp(SIGN 2 pi i r (j mod NS) / (NS R))
 // (the N-point twiddle table), takes the R-point DFT and writes
 // y[(j - j mod NS) R + j mod NS + r NS] through 'st'.  Thread t takes j = t + m T (T threads,
-// m < J); with 'inplace' every thread holds its values in registers across a barrier before
-// it stores, so that x and y may be the same buffer.
+// m < J; t = tid, the thread's index within the transform); with 'inplace' every thread holds
+// its values in registers across a barrier before it stores, so that x and y may be the same buffer.
 template <int LOGN, int P, int SIGN, class LD, class ST>
-__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD ld, ST st, bool inplace)
+__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD ld, ST st, bool inplace, int tid)
 {
     constexpr int N = 1 << LOGN, R = fft_radix(LOGN, P), NS = fft_ns(LOGN, P), T = fft_threads(N);
     constexpr int Q = N / R, TWS = N / (NS * R), J = (Q + T - 1) / T;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD 
 #pragma unroll
     for (int m = 0; m < J; ++m) {
         // past the row (small N only) a thread repeats the last element's loads and stores nothing
-        const int j = RAGGED ? min((int)threadIdx.x + m * T, Q - 1) : (int)threadIdx.x + m * T;
+        const int j = RAGGED ? min(tid + m * T, Q - 1) : tid + m * T;
         const int k = j & (NS - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[m][r] = ld(j + r * Q);
@@ -168,7 +168,7 @@ __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD 
     if (inplace) __syncthreads();
 #pragma unroll
     for (int m = 0; m < J; ++m) {
-        const int j = (int)threadIdx.x + m * T;
+        const int j = tid + m * T;
         if (!RAGGED || j < Q) {
             const int k = j & (NS - 1);
             const int o = (j - k) * R + k;
@@ -181,9 +181,10 @@ __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ tw, LD 
 // FFT of one row of 2^LOGN points by fft_threads(2^LOGN) threads: the passes from P on, the
 // first reading through 'gld', the last writing through 'gst', the ones in between in place in
 // the shared buffer 'buf' (padded by spad).  IN_SMEM / OUT_SMEM say that gld / gst touch 'buf'
-// themselves.  Ends with a barrier.
+// themselves.  tid: the thread's index within the transform (threadIdx.x when a block takes one
+// row).  Ends with a barrier of the whole block.
 template <int LOGN, int SIGN, bool IN_SMEM, bool OUT_SMEM, int P = 0, class LD, class ST>
-__device__ __forceinline__ void row_fft(const float2 *tw, float2 *buf, LD gld, ST gst)
+__device__ __forceinline__ void row_fft(const float2 *tw, float2 *buf, LD gld, ST gst, int tid = threadIdx.x)
 {
     constexpr int NP = fft_npass(LOGN);
     constexpr bool first = P == 0, last = P == NP - 1;
@@ -191,29 +192,16 @@ __device__ __forceinline__ void row_fft(const float2 *tw, float2 *buf, LD gld, S
     constexpr bool inplace = (src_smem && dst_smem) || NP == 1;
     auto sld = [&](int i) { return buf[spad(i)]; };
     auto sst = [&](int i, float2 v) { buf[spad(i)] = v; };
-    if constexpr (first && last) stockham_pass<LOGN, P, SIGN>(tw, gld, gst, inplace);
-    else if constexpr (first) stockham_pass<LOGN, P, SIGN>(tw, gld, sst, inplace);
-    else if constexpr (last) stockham_pass<LOGN, P, SIGN>(tw, sld, gst, inplace);
-    else stockham_pass<LOGN, P, SIGN>(tw, sld, sst, inplace);
+    if constexpr (first && last) stockham_pass<LOGN, P, SIGN>(tw, gld, gst, inplace, tid);
+    else if constexpr (first) stockham_pass<LOGN, P, SIGN>(tw, gld, sst, inplace, tid);
+    else if constexpr (last) stockham_pass<LOGN, P, SIGN>(tw, sld, gst, inplace, tid);
+    else stockham_pass<LOGN, P, SIGN>(tw, sld, sst, inplace, tid);
     __syncthreads();
-    if constexpr (P + 1 < NP) row_fft<LOGN, SIGN, IN_SMEM, OUT_SMEM, P + 1>(tw, buf, gld, gst);
+    if constexpr (P + 1 < NP) row_fft<LOGN, SIGN, IN_SMEM, OUT_SMEM, P + 1>(tw, buf, gld, gst, tid);
 }
 
 #define FFT_BOUNDS(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_REGS))
 #define FFT_BOUNDS_CONV(L) __launch_bounds__(fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS))
-
-// In-place FFT of row blockIdx.x of consecutive rows of 2^LOGN points, times 'scale'.
-template <int LOGN, int SIGN>
-__global__ void FFT_BOUNDS(LOGN) k_fft_rows(float2 *data, const float2 *__restrict__ tw, float scale)
-{
-    extern __shared__ float2 sm[];
-    {
-        const int row = blockIdx.x;   // one row per block (no loop: nothing is kept across rows)
-        float2 *d = data + ((size_t)row << LOGN);
-        row_fft<LOGN, SIGN, false, false>(tw, sm, [&](int i) { return d[i]; },
-                                    [&](int i, float2 v) { d[i] = make_float2(v.x * scale, v.y * scale); });
-    }
-}
 
 // GRF pass 1 (Eq. 4): for each spectrum row ky < ny, the unit-modulus random spectrum
 // exp(i xi) inside the elliptic passband 4 (kx^2 ny^2 + ky^2 nx^2) <= nx^2 ny^2 (integers, FFT
@@ -275,36 +263,67 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
     }
 }
 
-// ASM pass 2, on the transposed spectra (per field, one compact column of H values per spatial
-// frequency fx, 'rows' of them): zero-extension to 2^LOGN rows (the window at rows
-// oy .. oy + H - 1), forward FFT into shared memory, multiplication by the transfer function's
-// row (scale folded in), inverse FFT, and the window's rows stored back in place.  A block takes
-// one fx for all nf fields in turn, so that the transfer function's row is read from memory once.
-template <int LOGN>
-__global__ void FFT_BOUNDS_CONV(LOGN) k_asm_rows_conv(float2 *data, int rows, int H, int oy, int nf,
-                                                 const float2 *__restrict__ Ht, const float2 *__restrict__ tw)
+// Column transforms without transposes: a block takes C adjacent columns of a row-major array,
+// thread (c, t) = (threadIdx.x, threadIdx.y) being thread t of column c's transform, so that the
+// lanes of a warp read and write C consecutive elements of each row (C x 8 bytes: whole 32-byte
+// sectors for C >= 4).  Each column has its own shared buffer, C of them per block.
+// columns per block by transform length (measured on the 1080p ASM and the 4096x2048 GRF maps:
+// four columns of 4096 points, 1024 threads and 139 KB per block, ran 19 % slower than two)
+__host__ __device__ constexpr int cols_per_block(int logn) { return logn >= 12 ? 2 : logn >= 11 ? 4 : 8; }
+// float2 elements between the shared buffers of two columns: at least the padded row, and 8 mod
+// 16 so that two neighbouring columns start in opposite halves of the 32 banks
+__host__ __device__ constexpr int col_stride(int n) { return ((n + n / 16 + 1 + 15) / 16) * 16 + 8; }
+__host__ __device__ constexpr int cols_smem_bytes(int n, int c) { return c * col_stride(n) * (int)sizeof(float2); }
+#define COLS_BOUNDS(L, C) __launch_bounds__((C) * fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS * (C)))
+
+// ASM pass 2, on the compact spectra A (per field H rows of Wp, row-major): for C spatial
+// frequencies fx per block, the column of H values zero-extended to 2^LOGN rows (the window at
+// rows oy .. oy + H - 1), forward FFT in shared memory, multiplication by the transfer
+// function's row (scale folded in), inverse FFT, and the window's rows stored back in place.
+// Consecutive blocks take the same frequencies of the nf fields in turn, so that the transfer
+// function's rows are read from memory once.
+template <int LOGN, int C>
+__global__ void COLS_BOUNDS(LOGN, C) k_asm_cols(float2 *A, int Wp, int H, int oy, int nf,
+                                                const float2 *__restrict__ Ht, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 sm[];
-    {
-        const int it = blockIdx.x;    // one (frequency, field) per block
-        const int row = it / nf, f = it - row * nf;
-        float2 *d = data + ((size_t)f * rows + row) * H;
-        const float2 *h = Ht + ((size_t)row << LOGN);
-        row_fft<LOGN, -1, false, true>(tw, sm,
+    const int c = threadIdx.x, t = threadIdx.y;
+    const int grp = blockIdx.x / nf, f = blockIdx.x - grp * nf;
+    const int fx = grp * C + c;
+    float2 *col = A + (size_t)f * H * Wp + fx;           // row y at col[y * Wp]
+    float2 *buf = sm + c * col_stride(1 << LOGN);
+    const float2 *h = Ht + ((size_t)fx << LOGN);
+    row_fft<LOGN, -1, false, true>(tw, buf,
                                    [&](int i) {
                                        const int y = i - oy;
-                                       const float2 a = d[min(max(y, 0), H - 1)];                // in bounds
+                                       const float2 a = col[(size_t)min(max(y, 0), H - 1) * Wp];    // in bounds
                                        return (y >= 0 && y < H) ? a : make_float2(0.0f, 0.0f);
                                    },
-                                   [&](int i, float2 v) { sm[spad(i)] = v; });
-        for (int i = threadIdx.x; i < (1 << LOGN); i += blockDim.x) sm[spad(i)] = cmul(sm[spad(i)], __ldg(h + i));
-        __syncthreads();
-        row_fft<LOGN, +1, true, false>(tw, sm, [&](int i) { return sm[spad(i)]; },
+                                   [&](int i, float2 v) { buf[spad(i)] = v; }, t);
+    for (int i = t; i < (1 << LOGN); i += fft_threads(1 << LOGN)) buf[spad(i)] = cmul(buf[spad(i)], __ldg(h + i));
+    __syncthreads();
+    row_fft<LOGN, +1, true, false>(tw, buf, [&](int i) { return buf[spad(i)]; },
                                    [&](int i, float2 v) {
                                        const int y = i - oy;
-                                       if (y >= 0 && y < H) d[y] = v;
-                                   });
-    }
+                                       if (y >= 0 && y < H) col[(size_t)y * Wp] = v;
+                                   },
+                                   t);
+}
+
+// GRF pass 2 (Eq. 4): the unnormalised inverse FFT along y of C columns of the row pass's output
+// B [ny][nx] per block, its phase (atan2) stored to phi [ny][nx] row-major.
+template <int LOGN, int C>
+__global__ void COLS_BOUNDS(LOGN, C) k_grf_cols(const float2 *__restrict__ B, float *__restrict__ phi, int nx,
+                                                const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 sm[];
+    const int c = threadIdx.x, t = threadIdx.y;
+    const int ix = blockIdx.x * C + c;
+    const float2 *col = B + ix;
+    float *out = phi + ix;
+    float2 *buf = sm + c * col_stride(1 << LOGN);
+    row_fft<LOGN, +1, false, false>(tw, buf, [&](int i) { return col[(size_t)i * nx]; },
+                                    [&](int i, float2 v) { out[(size_t)i * nx] = atan2f(v.y, v.x); }, t);
 }
 
 // ASM pass 3: inverse FFT along x of the compact rows (H per field), cropped into the output
@@ -345,44 +364,6 @@ cudaError_t with_logn(int logn, F f)
     case 12: return f(std::integral_constant<int, 12>{});
     case 13: return f(std::integral_constant<int, 13>{});
     default: return cudaErrorInvalidValue;
-    }
-}
-
-// out[x][y] = in[y][x], in is h x w; blockIdx.z selects one of several w x h matrices stored
-// one after the other
-__global__ void k_transpose(const float2 *__restrict__ in, float2 *__restrict__ out, int w, int h)
-{
-    __shared__ float2 tile[32][33];
-    in += (size_t)blockIdx.z * w * h;
-    out += (size_t)blockIdx.z * w * h;
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int x = bx + threadIdx.x, y = by + k;
-        if (x < w && y < h) tile[k][threadIdx.x] = in[(size_t)y * w + x];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int x = by + threadIdx.x, y = bx + k;
-        if (x < h && y < w) out[(size_t)y * h + x] = tile[threadIdx.x][k];
-    }
-}
-
-// out[x][y] = arg(in[y][x]) (atan2f), in is h x w
-__global__ void k_transpose_arg(const float2 *__restrict__ in, float *__restrict__ out, int w, int h)
-{
-    __shared__ float tile[32][33];
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int x = bx + threadIdx.x, y = by + k;
-        if (x < w && y < h) {
-            const float2 v = in[(size_t)y * w + x];
-            tile[k][threadIdx.x] = atan2f(v.y, v.x);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int x = by + threadIdx.x, y = bx + k;
-        if (x < h && y < w) out[(size_t)y * h + x] = tile[threadIdx.x][k];
     }
 }
 
@@ -442,10 +423,16 @@ cudaError_t fft_setup()
         cudaError_t e = with_logn(l, [&](auto L) {
             constexpr int ll = decltype(L)::value;
             const int smem = fft_smem_bytes(1 << ll);
-            cudaError_t r = cudaFuncSetAttribute(k_fft_rows<ll, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_grf_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaError_t r = cudaFuncSetAttribute(k_grf_rows<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_in<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_conv<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            constexpr int cc = cols_per_block(ll);
+            const int csmem = cols_smem_bytes(1 << ll, cc);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_cols<ll, cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_grf_cols<ll, cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_cols<ll, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           cols_smem_bytes(1 << ll, 2));
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_grf_cols<ll, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           cols_smem_bytes(1 << ll, 2));
             if (r == cudaSuccess) r = cudaFuncSetAttribute(k_asm_rows_out<ll>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             return r;
         });
@@ -482,15 +469,15 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny;
     char *buf = nullptr;
-    const size_t bytes = 2 * n * sizeof(float2) + (size_t)(nx + ny) * sizeof(float2);
+    const size_t bytes = n * sizeof(float2) + (size_t)(nx + ny) * sizeof(float2);
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
-    float2 *A = (float2 *)buf, *B = A + n, *twx = B + n, *twy = twx + nx;
+    float2 *A = (float2 *)buf, *twx = A + n, *twy = twx + nx;
     cudaError_t e = cudaSuccess;
     k_twiddles<<<(nx + 255) / 256, 256, 0, s>>>(twx, nx);
     k_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(twy, ny);
-    // per map: spectrum generated and transformed along x, transpose, transform along y, the
-    // phase taken as the transpose back writes it
-    const dim3 tb(32, 8);
+    // per map: spectrum generated and transformed along x (row-major [ny][nx]), then the columns
+    // transformed along y with the phase taken as they are stored
+    const int ly = ilog2(ny);
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
         e = with_logn(ilog2(nx), [&](auto L) {
             constexpr int l = decltype(L)::value;
@@ -499,15 +486,16 @@ extern "C" hpt_status hpt_grf_build(hpt_ctx *ctx, uint64_t phase_seed, int32_t h
             return cudaGetLastError();
         });
         if (e != cudaSuccess) break;
-        k_transpose<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, s>>>(A, B, nx, ny);
-        e = with_logn(ilog2(ny), [&](auto L) {
+        e = with_logn(ly, [&](auto L) {
             constexpr int l = decltype(L)::value;
-            k_fft_rows<l, +1><<<nx, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(B, twy, 1.0f);
+            constexpr int cc = cols_per_block(l);
+            float *dst = phi_dev + (size_t)k * n;
+            if (nx >= cc)
+                k_grf_cols<l, cc><<<nx / cc, dim3(cc, fft_threads(1 << l)), cols_smem_bytes(1 << l, cc), s>>>(A, dst, nx, twy);
+            else
+                k_grf_cols<l, 2><<<nx / 2, dim3(2, fft_threads(1 << l)), cols_smem_bytes(1 << l, 2), s>>>(A, dst, nx, twy);
             return cudaGetLastError();
         });
-        if (e != cudaSuccess) break;
-        k_transpose_arg<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, s>>>(B, phi_dev + (size_t)k * n, ny, nx);
-        e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(buf, s);
     OPT_TRY(e);
@@ -520,17 +508,15 @@ namespace {
 // One padded angular-spectrum step of a W x H field: the sizes and the scratch it needs.
 struct AsmPlan {
     int W, H, Wp, Hp, lx, ly, ox, oy;
-    float2 *A, *B, *twx, *twy;
+    float2 *A, *twx, *twy;
 };
 
-// nf fields of one wavelength (consecutive W x H fields of 'in' and 'out'; P.A and P.B hold
-// nf x Wp x H each)
+// nf fields of one wavelength (consecutive W x H fields of 'in' and 'out'; P.A holds nf x Wp x H)
 cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, const float2 *Ht, cudaStream_t s)
 {
-    // the window's rows along x (H x Wp per field, compact) -> transpose (Wp x H) -> per-frequency
-    // columns zero-extended to Hp: FFT, transfer, inverse FFT, window rows kept -> transpose
-    // (H x Wp) -> inverse FFT along x, cropped
-    const dim3 tb(32, 8);
+    // the window's rows along x (H x Wp per field, compact, row-major) -> per-frequency columns
+    // zero-extended to Hp, read and written in place: FFT, transfer, inverse FFT, window rows kept
+    // -> inverse FFT along x, cropped
     const int rows = nf * P.H;
     cudaError_t e = with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
@@ -538,15 +524,18 @@ cudaError_t asm_field(const AsmPlan &P, const float2 *in, float2 *out, int nf, c
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
-    k_transpose<<<dim3((P.Wp + 31) / 32, (P.H + 31) / 32, nf), tb, 0, s>>>(P.A, P.B, P.Wp, P.H);
     e = with_logn(P.ly, [&](auto L) {
         constexpr int l = decltype(L)::value;
-        k_asm_rows_conv<l><<<P.Wp * nf, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(
-            P.B, P.Wp, P.H, P.oy, nf, Ht, P.twy);
+        constexpr int cc = cols_per_block(l);
+        if (P.Wp >= cc)
+            k_asm_cols<l, cc><<<(P.Wp / cc) * nf, dim3(cc, fft_threads(1 << l)), cols_smem_bytes(1 << l, cc), s>>>(
+                P.A, P.Wp, P.H, P.oy, nf, Ht, P.twy);
+        else
+            k_asm_cols<l, 2><<<(P.Wp / 2) * nf, dim3(2, fft_threads(1 << l)), cols_smem_bytes(1 << l, 2), s>>>(
+                P.A, P.Wp, P.H, P.oy, nf, Ht, P.twy);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
-    k_transpose<<<dim3((P.H + 31) / 32, (P.Wp + 31) / 32, nf), tb, 0, s>>>(P.B, P.A, P.H, P.Wp);
     return with_logn(P.lx, [&](auto L) {
         constexpr int l = decltype(L)::value;
         k_asm_rows_out<l><<<rows, fft_threads(1 << l), fft_smem_bytes(1 << l), s>>>(P.A, out, P.W, P.ox, P.twx);
@@ -717,13 +706,12 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     cudaStream_t s = (cudaStream_t)stream;
     const size_t np = (size_t)Wp * Hp;
     const int KB = std::min(K, ASM_BATCH);                 // fields per launch group
-    const size_t nab = std::max(np, (size_t)KB * Wp * H);
-    const size_t bytes = (2 * nab + (size_t)n_lambda * np + (size_t)(Wp + Hp)) * sizeof(float2);
+    const size_t na = (size_t)KB * Wp * H;
+    const size_t bytes = (na + (size_t)n_lambda * np + (size_t)(Wp + Hp)) * sizeof(float2);
     char *buf = nullptr;
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
     P.A = (float2 *)buf;
-    P.B = P.A + nab;
-    float2 *Hf = P.B + nab;
+    float2 *Hf = P.A + na;
     P.twx = Hf + (size_t)n_lambda * np;
     P.twy = P.twx + Wp;
     cudaError_t e = cudaSuccess;
@@ -763,14 +751,13 @@ extern "C" hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, flo
     OPT_TRY(cudaSetDevice(internal_ctx_device(ctx)));
     OPT_TRY(fft_setup());
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t np = (size_t)P.Wp * P.Hp, n = (size_t)W * H;
-    const size_t bytes = 4 * np * sizeof(float2) + (size_t)(P.Wp + P.Hp) * sizeof(float2) + 3 * n * sizeof(float2) +
+    const size_t np = (size_t)P.Wp * P.Hp, n = (size_t)W * H, na = (size_t)P.Wp * H;
+    const size_t bytes = (na + 2 * np) * sizeof(float2) + (size_t)(P.Wp + P.Hp) * sizeof(float2) + 3 * n * sizeof(float2) +
                          (3 * RED_BLOCKS + 2 + (size_t)std::max(iters, 1)) * sizeof(double);
     char *buf = nullptr;
     OPT_TRY(cudaMallocAsync((void **)&buf, bytes, s));
     P.A = (float2 *)buf;
-    P.B = P.A + np;
-    float2 *Hp_ = P.B + np, *Hm = Hp_ + np;          // transfer over +z and over -z (the adjoint)
+    float2 *Hp_ = P.A + na, *Hm = Hp_ + np;          // transfer over +z and over -z (the adjoint)
     P.twx = Hm + np;
     P.twy = P.twx + P.Wp;
     float2 *U = P.twy + P.Hp, *Afield = U + n, *V = Afield + n;
