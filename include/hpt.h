@@ -211,8 +211,9 @@ hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_
 /* Trace one frame like hpt_trace, without a captured graph, with a CUDA event recorded on the
  * context's wave stream before every launch, and report the device time and number of kernel
  * launches per kernel kind: HPT_K_GEN (primary path generation, with the queue-counter reset),
- * HPT_K_TRACE (BVH traversal of one queue iteration), HPT_K_SHADE (coherent and incoherent
- * shading of one iteration: two launches), HPT_K_ACCUM (Path-Reuse accumulation, Eq. 5).
+ * HPT_K_TRACE (BVH traversal of one queue iteration: two launches, coherent rays and incoherent /
+ * shadow rays), HPT_K_SHADE (coherent and incoherent shading of one iteration: two launches),
+ * HPT_K_ACCUM (Path-Reuse accumulation, Eq. 5).
  * Synchronous; the results in out_dev equal those of hpt_trace.  The paper has no counterpart:
  * this feeds the roofline of each kernel. */
 enum { HPT_K_GEN = 0, HPT_K_TRACE = 1, HPT_K_SHADE = 2, HPT_K_ACCUM = 3, HPT_NKERNELS = 4 };

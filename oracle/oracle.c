@@ -817,11 +817,15 @@ static double radiance(ctx_t *C, surf_t S, v3 wo, int v)
  *     relative change of L exceeds COND_KAPPA times the relative step;
  *   - P moved by COND_SPREAD steps the other way along both tangents: branch
  *     changes within the reach of float32 rounding, which the local probe misses.
- * The amplitude change sqrt(L') - sqrt(L), the local one scaled by COND_SPREAD
- * (a float32 path rounds its image point, its sampled directions and every hit
- * point: taken as at most that many steps together), bounds what the sample
- * may contribute to a disagreement; it is capped by sqrt(L) + sqrt(L'max),
- * the change when the path flips to the neighbouring branch. */
+ * The amplitude change sqrt(L') - sqrt(L), the local one scaled by COND_SPREAD,
+ * bounds what the sample may contribute to a disagreement; it is capped by
+ * sqrt(L) + sqrt(L'max), the change when the path flips to the neighbouring
+ * branch.  COND_SPREAD is the float32 budget of an incoherent path expressed as a
+ * move of its image point: the rounding of P to float32 (half an ulp), then at
+ * each of at most three incoherent vertices (depth 4) a few ulps of direction
+ * error (square root, sine and cosine, frame) carried over a hit distance of
+ * the order of |P|, and a few ulps of hit-point error: about 10 ulps per vertex,
+ * 32 in all. */
 #define COND_STEP   1.2e-7
 #define COND_KAPPA  30.0
 #define COND_SPREAD 32.0
@@ -1149,11 +1153,22 @@ typedef struct {
     const int64_t *cells;
     int64_t n;
     double *E;
+    double *sens;    /* optional [n][3]: sensitivity bound of each cell-channel */
     int64_t next;
     pthread_mutex_t mu;
 } bake_job_t;
 
-static void bake_cell(bake_job_t *J, int64_t cell, double E[3])
+/* radiance arriving at x from direction d (the first hit's incoherent radiance towards x), 0 on a miss */
+static double bake_sample(bake_job_t *J, v3 x, v3 d, int c, int64_t pix, int s)
+{
+    hit_t h;
+    if (!closest(J->o, x, d, 0.0, INFINITY, -1, 0, &h)) return 0.0;
+    surf_t S = surface(J->o, h.tri, add(x, scl(d, h.t)), h.b1, h.b2);
+    ctx_t C = {J->o, &J->r, c, c, s, pix, 0, 0, 0, 0.0, 0.0, 0.0};
+    return radiance(&C, S, scl(d, -1.0), 1);
+}
+
+static void bake_cell(bake_job_t *J, int64_t cell, double E[3], double sens[3])
 {
     const or_bake_desc *b = J->b;
     const int64_t R = b->res;
@@ -1163,20 +1178,33 @@ static void bake_cell(bake_job_t *J, int64_t cell, double E[3])
     for (int k = 0; k < 3; k++) xc[k] = b->bmin[k] + ((double)idx[k] + 0.5) * (b->bmax[k] - b->bmin[k]) / (double)R;
     const v3 x = mk(xc[0], xc[1], xc[2]);
     const int64_t pix = (iy + R * iz) * R + ix;
+    const double scale = fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z)));
     for (int c = 0; c < 3; c++) {
-        double acc = 0.0;
+        double acc = 0.0, dev = 0.0;
         for (int s = 0; s < b->spp; s++) {
             double u[4];
             path_draw(&J->r, c, pix, s, 0, 0, u);
             const double ct = 1.0 - 2.0 * u[0], st = 2.0 * sqrt(u[0] * (1.0 - u[0]));
             const v3 d = mk(st * cos(2.0 * PI * u[1]), st * sin(2.0 * PI * u[1]), ct);
-            hit_t h;
-            if (!closest(J->o, x, d, 0.0, INFINITY, -1, 0, &h)) continue;
-            surf_t S = surface(J->o, h.tri, add(x, scl(d, h.t)), h.b1, h.b2);
-            ctx_t C = {J->o, &J->r, c, c, s, pix, 0, 0, 0, 0.0, 0.0, 0.0};
-            acc += radiance(&C, S, scl(d, -1.0), 1);
+            const double L = bake_sample(J, x, d, c, pix, s);
+            acc += L;
+            if (sens) {
+                /* the sample's change when its start point moves by +-COND_SPREAD float32 ulps
+                   along two directions across the ray (the float32 budget of the path) */
+                double t3[3], b3[3], n3[3] = {d.x, d.y, d.z};
+                or_frame(n3, t3, b3);
+                double m = 0.0;
+                for (int k = 0; k < 4; k++) {
+                    const double *e = (k & 1) ? b3 : t3;
+                    const double step = ((k & 2) ? -1.0 : 1.0) * COND_SPREAD * COND_STEP * scale;
+                    const v3 x2 = add(x, scl(mk(e[0], e[1], e[2]), step));
+                    m = fmax(m, fabs(bake_sample(J, x2, d, c, pix, s) - L));
+                }
+                dev += m;
+            }
         }
         E[c] = PI * acc / (double)b->spp;
+        if (sens) sens[c] = PI * dev / (double)b->spp;
     }
 }
 
@@ -1190,19 +1218,25 @@ static void *bake_worker(void *arg)
         pthread_mutex_unlock(&J->mu);
         if (w >= J->n) break;
         int64_t end = w + 8 < J->n ? w + 8 : J->n;
-        for (int64_t i = w; i < end; i++) bake_cell(J, J->cells[i], J->E + 3 * i);
+        for (int64_t i = w; i < end; i++) bake_cell(J, J->cells[i], J->E + 3 * i, J->sens ? J->sens + 3 * i : NULL);
     }
     return NULL;
 }
 
 int or_bake(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, int n_threads)
 {
+    return or_bake_sens(h, b, cells, n_cells, E, NULL, n_threads);
+}
+
+int or_bake_sens(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, double *sens,
+                 int n_threads)
+{
     if (!h || !b || b->res < 1 || b->spp < 1 || b->max_depth < 1) return -1;
     for (int64_t i = 0; i < n_cells; i++)
         if (cells[i] < 0 || cells[i] >= (int64_t)b->res * b->res * b->res) return -2;
     bake_job_t J;
     memset(&J, 0, sizeof J);
-    J.o = h; J.b = b; J.cells = cells; J.n = n_cells; J.E = E;
+    J.o = h; J.b = b; J.cells = cells; J.n = n_cells; J.E = E; J.sens = sens;
     J.r.W = b->res; J.r.H = b->res * b->res; J.r.n_lambda = 3;
     for (int c = 0; c < 3; c++) J.r.channel[c] = c;
     J.r.spp = b->spp; J.r.max_depth = b->max_depth; J.r.K = 1; J.r.seed = b->seed;

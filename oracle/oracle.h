@@ -99,6 +99,12 @@ typedef struct {
     uint64_t seed;
 } or_bake_desc;
 int or_bake(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, int n_threads);
+/* or_bake plus sens [n_cells][3]: for each cell-channel, pi / spp times the sum over its
+ * directions of the largest change of the arriving radiance when the cell centre moves by 32
+ * float32 ulps (of its largest coordinate) along either of two directions across the ray, up or
+ * down -- the float32 budget of a GPU path, as for the trace's sensitivity bound. */
+int or_bake_sens(void *h, const or_bake_desc *b, const int64_t *cells, int64_t n_cells, double *E, double *sens,
+                 int n_threads);
 
 /* building blocks exposed for the pins */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -78,6 +78,8 @@ def _load():
             lib.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             lib.or_bake.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int]
             lib.or_bake.restype = C.c_int
+            lib.or_bake_sens.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int]
+            lib.or_bake_sens.restype = C.c_int
             lib.or_grf_phases.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
             lib.or_grf_phases.restype = None
             lib.or_cone_dir.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
@@ -203,8 +205,9 @@ class Oracle:
         U = out[..., 0] + 1j * out[..., 1]
         return (U, flags, sens) if with_flags else U
 
-    def bake(self, res, bmin, bmax, spp, max_depth, seed=1, cells=None, n_threads=None):
-        """Ambient cache E [n_cells][3] (float64) at the listed cell indices (all by default)."""
+    def bake(self, res, bmin, bmax, spp, max_depth, seed=1, cells=None, n_threads=None, with_sens=False):
+        """Ambient cache E [n_cells][3] (float64) at the listed cell indices (all by default);
+        with_sens: (E, sens), sens [n_cells][3] the float32-sensitivity bound of or_bake_sens."""
         if cells is None:
             cells = np.arange(res ** 3, dtype=np.int64)
         cells = np.ascontiguousarray(cells, np.int64)
@@ -213,11 +216,12 @@ class Oracle:
         for k in range(3):
             d.bmin[k], d.bmax[k] = float(bmin[k]), float(bmax[k])
         E = np.zeros((len(cells), 3), np.float64)
-        rc = self._lib.or_bake(self._h, C.byref(d), cells.ctypes.data, len(cells), E.ctypes.data,
-                               int(n_threads or os.cpu_count() or 1))
+        sens = np.zeros((len(cells), 3), np.float64) if with_sens else None
+        rc = self._lib.or_bake_sens(self._h, C.byref(d), cells.ctypes.data, len(cells), E.ctypes.data,
+                                    sens.ctypes.data if with_sens else None, int(n_threads or os.cpu_count() or 1))
         if rc != 0:
             raise ValueError(f"or_bake failed: {rc}")
-        return E
+        return (E, sens) if with_sens else E
 
     def trace_full(self, render, n_threads=None, grf=None):
         U = self.trace(render, None, n_threads, grf=grf)

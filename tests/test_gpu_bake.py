@@ -45,10 +45,12 @@ def test_bake_furnace(ctx, depth):
 
 def test_bake_matches_the_oracle(ctx, oracle_mod):
     """The cfg-1 scene (mirrors, glass, GGX, Lambert under one area light), 16^3 cells x RGB x
-    32 directions, depth 3: the same Philox draws on both sides, the GPU in float32.  Cells
-    whose rays pass curved mirrors and lenses are ill-conditioned (see the trace's parity
-    exception; some change branch and move a cell by a whole sample), so the bar is
-    statistical: 99 % of cell-channels within 1e-4, the grid mean within 5e-4."""
+    32 directions, depth 3: the same Philox draws on both sides, the GPU in float32 from the
+    cell centre on (a bake path has no coherent part).  The bar is the trace's, with the same
+    exception: a cell-channel beyond 1e-4 is excused only when the oracle finds it float32-
+    sensitive -- moving the cell centre within the 32-ulp float32 budget of a path changes it
+    by at least the tolerance -- and the disagreement stays within tolerance + that bound;
+    unexplained cell-channels <= 0.1 %."""
     sc = S.config1_scene()
     sid = ctx.upload_scene(sc)
     lo, hi = [-10 * MM, -3 * MM, 3 * MM], [10 * MM, 8 * MM, 32 * MM]
@@ -57,10 +59,19 @@ def test_bake_matches_the_oracle(ctx, oracle_mod):
     ctx.sync()
     got = E.cpu().numpy().reshape(-1, 3).astype(np.float64)
     lo32, hi32 = np.float32(lo).astype(np.float64), np.float32(hi).astype(np.float64)
-    ref = oracle_mod.Oracle(sc).bake(res, lo32, hi32, spp, depth, seed=11)
+    orc = oracle_mod.Oracle(sc)
+    ref = orc.bake(res, lo32, hi32, spp, depth, seed=11)
     scale = max(float(np.abs(ref).mean()), 1e-30)
-    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * scale)
-    assert np.mean(rel > 1e-4) <= 0.01, (np.mean(rel > 1e-4), rel.max())
+    tol = 1e-4 * np.maximum(np.abs(ref), 1e-3 * scale)
+    bad = np.abs(got - ref) > tol
+    cells = np.nonzero(bad.any(axis=1))[0]
+    _, sens = orc.bake(res, lo32, hi32, spp, depth, seed=11, cells=cells, with_sens=True)
+    sv = np.zeros_like(ref)
+    sv[cells] = sens
+    explained = bad & (sv >= tol) & (np.abs(got - ref) <= tol + sv)
+    unexplained = int((bad & ~explained).sum())
+    print(f"bake: {int(bad.sum())} of {bad.size} cell-channels beyond 1e-4, {unexplained} unexplained")
+    assert unexplained <= 1e-3 * bad.size, (int(bad.sum()), unexplained)
     assert abs(got.mean() - ref.mean()) <= 5e-4 * abs(ref.mean())
     ctx.release_scene(sid)
 

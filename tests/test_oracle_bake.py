@@ -66,3 +66,21 @@ def test_bake_subset_equals_full_grid(oracle_mod):
     sub = o.bake(4, lo, hi, 4, 3, seed=5, cells=cells)
     assert np.array_equal(sub, full[cells])
     assert np.all(full >= 0) and full.max() > 0
+
+
+def test_bake_sensitivity_bound(oracle_mod):
+    """The float32-sensitivity bound of the bake: zero where the arriving radiance does not
+    depend on the start point (the furnace: every direction brings the same radiance), and below
+    a square emitter only the directions that pass within a few float32 ulps of its edges count,
+    each by at most its full radiance: 0 <= sens <= pi Le, and the values E are those of or_bake."""
+    rho, Le = 0.5, 1.0
+    o = oracle_mod.Oracle(S.furnace_scene(albedo=rho, Le=Le))
+    E, sens = o.bake(3, [-3 * MM, -3 * MM, -1 * MM], [3 * MM, 3 * MM, 5 * MM], 8, 3, seed=9, with_sens=True)
+    assert np.all(sens == 0.0)
+    assert np.array_equal(E, o.bake(3, [-3 * MM, -3 * MM, -1 * MM], [3 * MM, 3 * MM, 5 * MM], 8, 3, seed=9))
+    Le = 2.0
+    o = oracle_mod.Oracle(S.emissive_plane_scene(z=5 * MM, half=3 * MM, Le=Le))
+    E, sens = o.bake(2, [-4 * MM, -2 * MM, 0.0], [4 * MM, 6 * MM, 4 * MM], 512, 1, seed=3, with_sens=True)
+    assert np.all(sens >= 0.0) and np.all(sens <= math.pi * Le)
+    # a direction within 32 ulps (~4e-6 relative) of an edge is rare among 512 uniform ones
+    assert np.median(sens / np.maximum(E, 1e-30)) < 1e-2
