@@ -267,13 +267,18 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
 // thread (c, t) = (threadIdx.x, threadIdx.y) being thread t of column c's transform, so that the
 // lanes of a warp read and write C consecutive elements of each row (C x 8 bytes: whole 32-byte
 // sectors for C >= 4).  Each column has its own shared buffer, C of them per block.
-// columns per block by transform length (measured on the 1080p ASM and the 4096x2048 GRF maps:
-// four columns of 4096 points, 1024 threads and 139 KB per block, ran 19 % slower than two)
-__host__ __device__ constexpr int cols_per_block(int logn) { return logn >= 12 ? 2 : logn >= 11 ? 4 : 8; }
-// float2 elements between the shared buffers of two columns: at least the padded row, and 8 mod
-// 16 so that two neighbouring columns start in opposite halves of the 32 banks
-__host__ __device__ constexpr int col_stride(int n) { return ((n + n / 16 + 1 + 15) / 16) * 16 + 8; }
-__host__ __device__ constexpr int cols_smem_bytes(int n, int c) { return c * col_stride(n) * (int)sizeof(float2); }
+// columns per block by transform length, as measured on the GB300: two, except four for 2048
+// points (the 4096x2048 GRF maps: 0.81 ms against 0.91 with two and 0.99 with eight); four
+// columns of 4096 points (1024 threads, 139 KB per block, one block per SM) ran 19 % slower than
+// two on the 1080p ASM, eight columns of 1024 points 24 % slower than two on the 1920x270 one
+__host__ __device__ constexpr int cols_per_block(int logn) { return logn == 11 ? 4 : 2; }
+// float2 elements between the shared buffers of two of C columns: at least the padded row, plus
+// 8 (4 for eight columns), so that the columns a warp's lanes touch start in different banks
+__host__ __device__ constexpr int col_stride(int n, int c) { return ((n + n / 16 + 1 + 15) / 16) * 16 + (c >= 8 ? 4 : 8); }
+__host__ __device__ constexpr int cols_smem_bytes(int n, int c) { return c * col_stride(n, c) * (int)sizeof(float2); }
+static_assert(cols_per_block(13) * fft_threads(1 << 13) <= 1024 && cols_smem_bytes(1 << 13, cols_per_block(13)) <= 227 * 1024,
+              "column blocks of 8192 points exceed a block's threads or shared memory");
+
 #define COLS_BOUNDS(L, C) __launch_bounds__((C) * fft_threads(1 << (L)), fft_minb(1 << (L), HPT_FFT_CONV_REGS * (C)))
 
 // ASM pass 2, on the compact spectra A (per field H rows of Wp, row-major): for C spatial
@@ -291,7 +296,7 @@ __global__ void COLS_BOUNDS(LOGN, C) k_asm_cols(float2 *A, int Wp, int H, int oy
     const int grp = blockIdx.x / nf, f = blockIdx.x - grp * nf;
     const int fx = grp * C + c;
     float2 *col = A + (size_t)f * H * Wp + fx;           // row y at col[y * Wp]
-    float2 *buf = sm + c * col_stride(1 << LOGN);
+    float2 *buf = sm + c * col_stride(1 << LOGN, C);
     const float2 *h = Ht + ((size_t)fx << LOGN);
     row_fft<LOGN, -1, false, true>(tw, buf,
                                    [&](int i) {
@@ -321,7 +326,7 @@ __global__ void COLS_BOUNDS(LOGN, C) k_grf_cols(const float2 *__restrict__ B, fl
     const int ix = blockIdx.x * C + c;
     const float2 *col = B + ix;
     float *out = phi + ix;
-    float2 *buf = sm + c * col_stride(1 << LOGN);
+    float2 *buf = sm + c * col_stride(1 << LOGN, C);
     row_fft<LOGN, +1, false, false>(tw, buf, [&](int i) { return col[(size_t)i * nx]; },
                                     [&](int i, float2 v) { out[(size_t)i * nx] = atan2f(v.y, v.x); }, t);
 }
