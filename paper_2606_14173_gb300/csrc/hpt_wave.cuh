@@ -235,6 +235,9 @@ __device__ __forceinline__ bool exact_hit(const DevScene &sc, int tri, const R3<
 #ifndef HPT_SHADE_MINB
 #define HPT_SHADE_MINB 8            // 64 registers: 50 % occupancy beats the spill-free 96 (31 %)
 #endif
+#ifndef HPT_SHADE_INC_MINB
+#define HPT_SHADE_INC_MINB HPT_SHADE_MINB   // the incoherent shading kernel
+#endif
 #ifndef HPT_TRACE_MINB
 #define HPT_TRACE_MINB 8
 #endif
@@ -499,7 +502,7 @@ __device__ __forceinline__ bool vertex(const PathId &id, IncState &st, const Sur
 // COH = true: the coherent entries of the iteration; false: the incoherent ones (two kernels,
 // so that each carries only its half of the shading code)
 template <class R, bool STATS, bool COH>
-__global__ void __launch_bounds__(SHADE_BLOCK, HPT_SHADE_MINB) k_shade(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
+__global__ void __launch_bounds__(SHADE_BLOCK, COH ? HPT_SHADE_MINB : HPT_SHADE_INC_MINB) k_shade(const JobTable *__restrict__ jt, const WaveDesc wd, PathBufs pb,
                                                        SlotScratch *__restrict__ scr, int it)
 {
     using RO = RealOps<R>;
