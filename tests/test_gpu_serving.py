@@ -72,6 +72,41 @@ def test_results_alone_and_in_the_mix(torch_cuda):
         ctx.close()
 
 
+def test_config4_requests_alone_and_in_the_mix(torch_cuda):
+    """Requests drawn by the config-4 recipe (each config's scene, pitch, wavelengths and depth, the
+    185k-triangle scene with its ambient cache resident, poses and focal depths), shrunk to small
+    SLMs and sample counts: library-owned outputs, each bit-identical to the same render traced
+    alone."""
+    from paper_2606_14173_gb300 import hpt
+    ctx = hpt.Context(0)
+    try:
+        sids = {"cfg0": ctx.upload_scene(S.config0_scene()), "cfg1": ctx.upload_scene(S.config1_scene()),
+                "cfg3": ctx.upload_scene(S.config3_scene())}
+        reqs = []
+        for key, r in S.config4_requests(40, seed=77):
+            r.W, r.H, r.spp = max(8, r.W // 16), max(8, r.H // 16), max(2, r.spp // 16)
+            reqs.append((key, r))
+            if len(reqs) == 8:
+                break
+        assert {k for k, _ in reqs} >= {"cfg1", "cfg3"}
+        alone = []
+        for key, r in reqs:
+            out = hpt.alloc_output(r)
+            ctx.trace(sids[key], r, out)
+            ctx.sync()
+            alone.append(out.cpu().numpy())
+        ids = [ctx.submit(sids[key], r, None) for key, r in reqs]
+        for i, (key, r), ref in zip(ids, reqs, alone):
+            ctx.wait(i, 120000)
+            got = np.empty(r.out_shape(), np.complex64)
+            ctx.request_output(i, got)
+            ctx.request_release(i)
+            assert np.array_equal(got, ref), f"{key} {r.W}x{r.H} spp {r.spp} K {r.K} differs in the mix"
+        ctx.sync()
+    finally:
+        ctx.close()
+
+
 def test_admission_by_memory_budget(torch_cuda):
     """With a budget smaller than two outputs, requests run one after another."""
     from paper_2606_14173_gb300 import hpt
