@@ -253,32 +253,58 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
 // Double-precision closest hit used when the float traversal of a coherent ray was not
 // conclusive.  Exact triangle edges (from the float32 vertices), Moller-Trumbore in double,
 // ties to the lower triangle id -- the decision rule of the definition.
+//
+// The box tests need not be exact, only conservative: every box the double ray meets at some t
+// in [0, best] must be visited, and which boxes are visited changes the work, never the winner.
+// They run in float against the boxes widened by w = 2^-17 (|o|_inf + M), M the largest
+// coordinate magnitude of the scene's bounds.  For a point X = o + t d inside the bounds, the
+// float ray (o and d rounded to float) passes within 2^-24 (|o|_inf + |X - o|_inf) <=
+// 2^-24 (2 |o|_inf + M) of X, and the slab arithmetic (the rounded reciprocal, the rounded
+// origin products, one FMA) errs by a few units of 2^-24 (|o|_inf + M) in space; w covers both
+// with a margin of about 8.  Culling uses the double best rounded up to float with a margin of
+// 2^-16.  (GB300 runs float at 64 times the double rate; the boxes are most of the work.)
 template <int SSTRIDE>
 __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double oy, double oz, double dx, double dy,
                                           double dz, double tmin, int skip, double *t_out, int *stk, int slimit,
                                           int &status)
 {
-    double ix = fabs(dx) > 1e-300 ? 1.0 / dx : 1e300, iy = fabs(dy) > 1e-300 ? 1.0 / dy : 1e300,
-           iz = fabs(dz) > 1e-300 ? 1.0 / dz : 1e300;
+    const float3 of = f3((float)ox, (float)oy, (float)oz);
+    const float3 dfl = f3((float)dx, (float)dy, (float)dz);
+    float M;
+    {
+        const float4 r0 = __ldg(sc.nodes), r1 = __ldg(sc.nodes + 1), r2 = __ldg(sc.nodes + 2);
+        M = fmaxf(fmaxf(fmaxf(fabsf(r0.x), fabsf(r0.y)), fmaxf(fabsf(r0.z), fabsf(r0.w))),
+                  fmaxf(fmaxf(fabsf(r1.x), fabsf(r1.y)), fmaxf(fabsf(r1.z), fabsf(r1.w))));
+        M = fmaxf(M, fmaxf(fmaxf(fabsf(r2.x), fabsf(r2.y)), fmaxf(fabsf(r2.z), fabsf(r2.w))));
+    }
+    const float w = (fmaxf(fmaxf(fabsf(of.x), fabsf(of.y)), fabsf(of.z)) + M) * 0x1p-17f;
+    const float3 inv = f3(fabsf(dfl.x) > 1e-20f ? 1.0f / dfl.x : copysignf(1e20f, dfl.x),
+                          fabsf(dfl.y) > 1e-20f ? 1.0f / dfl.y : copysignf(1e20f, dfl.y),
+                          fabsf(dfl.z) > 1e-20f ? 1.0f / dfl.z : copysignf(1e20f, dfl.z));
+    // lower planes moved down by w, upper planes up by w: (lo - w - o) inv = lo inv - (o + w) inv
+    const float3 oa = f3((of.x + w) * inv.x, (of.y + w) * inv.y, (of.z + w) * inv.z);
+    const float3 ob = f3((of.x - w) * inv.x, (of.y - w) * inv.y, (of.z - w) * inv.z);
     double best = 1e300;
     int best_id = -1;
+    float tl = 1e30f;
     int sp = 0, node = 0;
     for (;;) {
         while (node >= 0) {
+            // 16-byte loads: ptxas of CUDA 13.0 fails on the 32-byte form in this non-inlined function
             const float4 *np = sc.nodes + 4 * node;
-            float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
-            double lo0[3] = {n0.x, n0.z, n2.x}, hi0[3] = {n0.y, n0.w, n2.y};
-            double lo1[3] = {n1.x, n1.z, n2.z}, hi1[3] = {n1.y, n1.w, n2.w};
+            const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+            const float a0 = fmaf(n0.x, inv.x, -oa.x), b0 = fmaf(n0.y, inv.x, -ob.x);
+            const float a1 = fmaf(n0.z, inv.y, -oa.y), b1 = fmaf(n0.w, inv.y, -ob.y);
+            const float a2 = fmaf(n2.x, inv.z, -oa.z), b2 = fmaf(n2.y, inv.z, -ob.z);
+            const float e0 = fmaf(n1.x, inv.x, -oa.x), f0 = fmaf(n1.y, inv.x, -ob.x);
+            const float e1 = fmaf(n1.z, inv.y, -oa.y), f1 = fmaf(n1.w, inv.y, -ob.y);
+            const float e2 = fmaf(n2.z, inv.z, -oa.z), f2 = fmaf(n2.w, inv.z, -ob.z);
             const int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
-            double o[3] = {ox, oy, oz}, iv[3] = {ix, iy, iz};
-            double t0a = 0.0, t0b = best * (1.0 + 1e-9), t1a = 0.0, t1b = best * (1.0 + 1e-9);
-            for (int k = 0; k < 3; ++k) {
-                double a = (lo0[k] - o[k]) * iv[k], b = (hi0[k] - o[k]) * iv[k];
-                t0a = fmax(t0a, fmin(a, b)); t0b = fmin(t0b, fmax(a, b));
-                a = (lo1[k] - o[k]) * iv[k]; b = (hi1[k] - o[k]) * iv[k];
-                t1a = fmax(t1a, fmin(a, b)); t1b = fmin(t1b, fmax(a, b));
-            }
-            bool h0 = t0a <= t0b, h1 = t1a <= t1b;
+            const float t0a = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            const float t0b = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tl));
+            const float t1a = fmaxf(fmaxf(fminf(e0, f0), fminf(e1, f1)), fmaxf(fminf(e2, f2), 0.0f));
+            const float t1b = fminf(fminf(fmaxf(e0, f0), fmaxf(e1, f1)), fminf(fmaxf(e2, f2), tl));
+            const bool h0 = t0a <= t0b, h1 = t1a <= t1b;
             if (!h0 && !h1) {
                 if (sp == 0) { *t_out = best; return best_id; }
                 node = stk[(--sp) * SSTRIDE];
@@ -312,7 +338,11 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
             double v = (dx * qx + dy * qy + dz * qz) * id_;
             double t = (e2x * qx + e2y * qy + e2z * qz) * id_;
             if (u < 0.0 || v < 0.0 || u + v > 1.0 || !(t > tmin)) continue;
-            if (t < best || (t == best && id < best_id)) { best = t; best_id = id; }
+            if (t < best || (t == best && id < best_id)) {
+                best = t;
+                best_id = id;
+                tl = __double2float_ru(best) * (1.0f + 0x1p-16f);
+            }
         }
         if (sp == 0) break;
         node = stk[(--sp) * SSTRIDE];
