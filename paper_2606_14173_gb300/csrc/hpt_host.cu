@@ -620,6 +620,44 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     }
     const int n_knodes = (int)(knodes.size() / 4);
     const int n_order = (int)order.size();
+    {
+        // the first TOP_ORDER inner nodes breadth-first from the root, the others in their
+        // depth-first order; the links are renumbered (the tree itself is unchanged)
+        const int ntop = std::min(n_knodes, TOP_ORDER);
+        std::vector<int> bfs;
+        std::vector<char> top(n_knodes, 0);
+        bfs.reserve(ntop);
+        bfs.push_back(0);
+        top[0] = 1;
+        for (size_t h = 0; h < bfs.size() && (int)bfs.size() < ntop; ++h) {
+            int link[2];
+            memcpy(&link[0], &knodes[4 * (size_t)bfs[h] + 3].x, 4);
+            memcpy(&link[1], &knodes[4 * (size_t)bfs[h] + 3].y, 4);
+            for (int c = 0; c < 2; ++c)
+                if (link[c] >= 0 && (int)bfs.size() < ntop) {
+                    bfs.push_back(link[c]);
+                    top[link[c]] = 1;
+                }
+        }
+        std::vector<int> nid(n_knodes);
+        int k = 0;
+        for (int n : bfs) nid[n] = k++;
+        for (int n = 0; n < n_knodes; ++n)
+            if (!top[n]) nid[n] = k++;
+        std::vector<float4> re(knodes.size());
+        for (int n = 0; n < n_knodes; ++n) {
+            float4 *o = &re[4 * (size_t)nid[n]];
+            for (int j = 0; j < 4; ++j) o[j] = knodes[4 * (size_t)n + j];
+            int link[2];
+            memcpy(&link[0], &o[3].x, 4);
+            memcpy(&link[1], &o[3].y, 4);
+            for (int c = 0; c < 2; ++c)
+                if (link[c] >= 0) link[c] = nid[link[c]];
+            memcpy(&o[3].x, &link[0], 4);
+            memcpy(&o[3].y, &link[1], 4);
+        }
+        knodes.swap(re);
+    }
 
     // triangle records
     std::vector<float4> tri4(3 * (size_t)std::max(n_order, 1));

@@ -14,6 +14,9 @@ constexpr int KMAX = 8;            // holograms per path set (Path Reuse)
 #define HPT_TSTACK 32
 #endif
 constexpr int TSTACK = HPT_TSTACK; // most traversal stack entries per thread (shared memory)
+// the first BVH nodes are laid out breadth-first from the root (the rest depth-first): the
+// levels every ray visits first share a few KB of cache lines
+constexpr int TOP_ORDER = 255;
 constexpr int TRACE_BLOCK = 128;   // threads per block of the trace kernel
 constexpr int SHADE_BLOCK = 128;
 constexpr int GEN_BLOCK = 256;
