@@ -551,7 +551,7 @@ def main():
             ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
         barrier(world)
         t0 = time.perf_counter()
-        k_e2e = max(2, args.steps // 2)
+        k_e2e = max(3, args.steps)
         for _ in range(k_e2e):
             ctx.trace_host(sid, r, host, precision=hpt.PREC_DF32, stream=stream)
         e2e_s = allreduce_max(time.perf_counter() - t0, world)

@@ -256,8 +256,8 @@ __global__ void FFT_BOUNDS(LOGN) k_asm_rows_in(const float2 *__restrict__ in, fl
         row_fft<LOGN, -1, false, false>(tw, sm,
                                     [&](int i) {
                                         const int x = i - ox;
-                                        const float2 a = __ldg(src + min(max(x, 0), W - 1));   // in bounds
-                                        return (x >= 0 && x < W) ? a : make_float2(0.0f, 0.0f);
+                                        // only the window's points are loaded (a predicated load)
+                                        return (x >= 0 && x < W) ? __ldg(src + x) : make_float2(0.0f, 0.0f);
                                     },
                                     [&](int i, float2 v) { d[i] = v; });
     }
@@ -301,8 +301,8 @@ __global__ void COLS_BOUNDS(LOGN, C) k_asm_cols(float2 *A, int Wp, int H, int oy
     row_fft<LOGN, -1, false, true>(tw, buf,
                                    [&](int i) {
                                        const int y = i - oy;
-                                       const float2 a = col[(size_t)min(max(y, 0), H - 1) * Wp];    // in bounds
-                                       return (y >= 0 && y < H) ? a : make_float2(0.0f, 0.0f);
+                                       // only the window's rows are loaded (a predicated load)
+                                       return (y >= 0 && y < H) ? col[(size_t)y * Wp] : make_float2(0.0f, 0.0f);
                                    },
                                    [&](int i, float2 v) { buf[spad(i)] = v; }, t);
     for (int i = t; i < (1 << LOGN); i += fft_threads(1 << LOGN)) buf[spad(i)] = cmul(buf[spad(i)], __ldg(h + i));
