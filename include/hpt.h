@@ -206,8 +206,9 @@ hpt_status hpt_sync(hpt_ctx *ctx);
  * coherent refinements, FP64 fallback traversals, NEE shadow rays, BSDF bounces.
  * The trace runs on separately compiled counting kernels: the fields they write to out_dev
  * meet the parity tolerance but may differ from hpt_trace's in the last bits (the counter
- * updates split the shading code where the compiler fuses multiply-adds), and through such a
- * rounding difference an incoherent path may occasionally take another branch. */
+ * updates change the code around them, and with it where the compiler fuses multiply-adds),
+ * and through such a rounding difference an incoherent path may occasionally take another
+ * branch. */
 enum { HPT_NCOUNTERS = 8 };
 hpt_status hpt_trace_counters(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                               void *out_dev, size_t out_bytes, uint64_t counters[HPT_NCOUNTERS]);
