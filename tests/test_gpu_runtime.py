@@ -136,6 +136,27 @@ def test_timed_trace_reports_kernels_and_keeps_results(torch_cuda):
         ctx.close()
 
 
+def test_counting_trace_meets_the_bar_against_the_trace(torch_cuda):
+    """hpt_trace_counters runs separately compiled counting kernels: its fields need not be the
+    trace's bit for bit, but they meet the parity bar against them, and its counts are those of
+    the render (one path sample per (lambda, pixel, sample), at least one ray each)."""
+    from paper_2606_14173_gb300 import hpt
+    from tests.parity import assert_parity
+    ctx = hpt.Context(0)
+    try:
+        sid = ctx.upload_scene(S.config1_scene())
+        r = S.config1_render(W=320, H=180, spp=8, K=4)
+        out = hpt.alloc_output(r)
+        ref = _trace(ctx, sid, r, out)
+        c = ctx.trace_counters(sid, r, out)
+        assert_parity(out.cpu().numpy(), ref, "counting trace")
+        assert c["samples"] == r.path_samples()
+        assert c["rays"] >= c["samples"] and c["box_tests"] > c["rays"] and c["tri_tests"] > 0
+        assert c["shadow_rays"] + c["bounces"] <= c["rays"]
+    finally:
+        ctx.close()
+
+
 def test_many_waves_over_lanes_graph_and_direct(torch_cuda, oracle_mod):
     """A frame split into many small waves (65536 paths each) rotates over the wave lanes, in a
     captured graph and in direct launches: the two agree bit for bit and match the oracle."""
