@@ -4,10 +4,11 @@
 // Both rest on one 2-D FFT of power-of-two sizes: every row transformed in shared memory by
 // one block (Stockham autosort: radix-16 passes in registers, the remainder radix first, the
 // first pass reading global memory and the last writing it in natural order, the passes in
-// between in place in one bank-padded shared buffer), a tiled transpose, the rows again, and
-// the transpose back.  Work around the transforms is folded into them: the GRF spectrum is
-// generated as the first pass loads it and the phase taken as the last transpose stores it;
-// the ASM's zero padding is never stored (see asm_field).  The data are complex64; the twiddle factors are rounded from
+// between in place in one bank-padded shared buffer), then every column the same way, a few
+// adjacent columns per block read and written in place in the row-major array (no transposes).
+// Work around the transforms is folded into them: the GRF spectrum is generated as the row
+// pass loads it and the phase taken as the column pass stores it; the ASM's zero padding is
+// never stored (see asm_field).  The data are complex64; the twiddle factors are rounded from
 // double-precision values.  The transfer function's phase 2 pi z sqrt(1/lambda^2 - f^2),
 // ~1e5 turns, is formed in double-float arithmetic before its fraction is taken.
 #include <algorithm>
@@ -237,9 +238,9 @@ __global__ void FFT_BOUNDS(LOGN) k_grf_rows(float2 *out, int ny, unsigned m, uns
 }
 
 // The ASM's 2-D transforms skip the zero padding: only the H rows of the window are transformed
-// along x, kept compact (H rows of n_x), transposed to n_x columns of H, and each column is
-// zero-extended to n_y as it is loaded and only its window rows are stored after the inverse
-// transform; the rows outside the window are never written nor read.
+// along x, kept compact (H rows of n_x, row-major); the column pass reads each column of that
+// array in place, zero-extends it to n_y as it loads it and stores only its window rows after
+// the inverse transform; the rows outside the window are never written nor read.
 
 // ASM pass 1: forward FFT along x of the window's rows, zero-padded to 2^LOGN: out[y][k] for
 // row y = blockIdx.x (the H rows of each of the fields, one field after the other), from
