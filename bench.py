@@ -52,6 +52,12 @@ FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "ho
 # the headline frame (the traffic is per ray), copied here: the bench cannot read hardware
 # counters itself.  None whenever k_trace changed since that capture.
 TRACE_DRAM_BYTES_PER_LAUNCH = 138e6
+# Issue counters of the two trace kernels from one ncu --set full capture each on the same band
+# (coherent rays at iteration 0, incoherent and shadow rays at iteration 1), copied here for the
+# same reason: threads active per issued warp instruction (smsp__thread_inst_executed_per_inst_
+# executed / 32) and issue activity (smsp__issue_active).  None whenever k_trace changed since.
+TRACE_ISSUE = {"simt_efficiency": {"coherent": 12.42 / 32, "incoherent_shadow": 13.44 / 32},
+               "issue_active": {"coherent": 0.615, "incoherent_shadow": 0.662}}
 
 
 # name -> (description, scene factory, render factory)
@@ -584,6 +590,9 @@ def main():
                 "traffic_source": ("ncu capture of both trace kernels on the 1920x270 band with 2M-path waves, "
                                    "scaled x4.0 to the 8M-path waves of this frame" if traffic is not None else None),
                 "kernel": "k_trace",
+                "issue": TRACE_ISSUE if args.workload in ("cfg2", "band") else None,
+                "issue_source": ("ncu --set full capture of each trace kernel on the 1920x270 band with "
+                                 "2M-path waves" if args.workload in ("cfg2", "band") else None),
                 "measured_probes": probes,
                 "frac_of_measured_fp32": (achieved / probes["fp32_tflops"]) if probes else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no measured FP32 peak)",
