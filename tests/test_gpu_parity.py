@@ -212,7 +212,12 @@ def test_config3_cache_scene_crop(ctx, cfg3, use_cache):
     r = S.config3_render(W=157, H=93, spp=8, K=2, use_cache=use_cache)
     ref, flags, sens = orc.trace(r, with_flags=True)
     ref = ref.reshape(3, 2, r.H, r.W)
-    assert_parity_explained(gpu_trace(ctx, sid, r, 1), ref, flags, sens, f"cfg3 crop cache={use_cache}")
+    reps = assert_parity_explained(gpu_trace(ctx, sid, r, 1), ref, flags, sens, f"cfg3 crop cache={use_cache}",
+                                   sensitive_only=True)
+    # the exception is no blanket waiver: the pixels out of the bar are a few per cent of the
+    # pixels whose field the oracle finds float32-sensitive, not most of them
+    for rep in reps:
+        assert rep["failing"] <= 0.1 * rep["sensitive_frac"] * rep["n"] + 2, rep
 
 
 def test_config3_full_size_sampled(ctx, cfg3):
