@@ -11,6 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libhpt.so")
+# the checked build: the same sources with every device index checked (-DHPT_CHECKED=1), for tests
+LIB_CHECKED = os.path.join(LIBDIR, "libhpt_checked.so")
 SOURCES = ["hpt_host.cu", "hpt_kernel.cu", "hpt_wave_f64.cu", "hpt_wave_df.cu", "hpt_static.cu", "hpt_optics.cu", "hpt_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -27,17 +29,19 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps():
+        return lib
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = _nvcc()
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                    "-I", CSRC] + os.environ.get("HPT_NVCC_FLAGS", "").split()
+                    "-I", CSRC] + os.environ.get("HPT_NVCC_FLAGS", "").split() + (["-DHPT_CHECKED=1"] if checked else [])
     objs = []
+    tag = "c" if checked else "p"
 
     def comp(src):
-        obj = os.path.join(LIBDIR, src.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(LIBDIR, src.replace(".cu", f".{tag}{os.getpid()}.o"))
         cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
@@ -51,15 +55,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -163,6 +163,11 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     int LEAF = 0;                   // pending leaf (< 0); 0 = none (the root is never a leaf)
     for (;;) {
         while (node >= 0 && node != SENT) {
+            if (!HPT_IN(node, sc.n_nodes)) {
+                status |= ST_BOUNDS;
+                node = SENT;
+                break;
+            }
             float tl = h.t * cull;
             const float4 *np = nodes + 4 * node;
             float4 n0, n1, n2, n3;
@@ -202,12 +207,20 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
             // leaf: ~(start << 8 | count)
             int code = ~LEAF;
             int start = code >> 8, count = code & 255;
+            if (count > 0 && !HPT_IN(start + count - 1, sc.n_tri4)) {
+                status |= ST_BOUNDS;
+                count = 0;
+            }
             for (int i = start; i < start + count; ++i) {
                 const float4 *tp = tris + 3 * i;
                 float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
                 int id = __float_as_int(A.w);
                 if (STATS) cnt.tris++;
                 if (id == skip) continue;
+                if (!HPT_IN(id, sc.n_tris)) {
+                    status |= ST_BOUNDS;
+                    continue;
+                }
                 float3 e1 = xyz(E1), e2 = xyz(E2);
                 float3 pv = cross3_rn(d, e2);
                 float det = dot3_rn(e1, pv);
@@ -290,6 +303,11 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
     int sp = 0, node = 0;
     for (;;) {
         while (node >= 0) {
+            if (!HPT_IN(node, sc.n_nodes)) {
+                status |= ST_BOUNDS;
+                *t_out = best;
+                return best_id;
+            }
             // 16-byte loads: ptxas of CUDA 13.0 fails on the 32-byte form in this non-inlined function
             const float4 *np = sc.nodes + 4 * node;
             const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
@@ -320,9 +338,17 @@ __device__ __noinline__ int traverse_fp64(const DevScene &sc, double ox, double 
         }
         int code = ~node;
         int start = code >> 8, count = code & 255;
+        if (count > 0 && !HPT_IN(start + count - 1, sc.n_tri4)) {
+            status |= ST_BOUNDS;
+            count = 0;
+        }
         for (int i = start; i < start + count; ++i) {
             int id = __float_as_int(__ldg(sc.tri4 + 3 * i).w);
             if (id == skip) continue;
+            if (!HPT_IN(id, sc.n_tris)) {
+                status |= ST_BOUNDS;
+                continue;
+            }
             uint4 ix4 = __ldg(sc.tri_attr + id);
             const float *p0 = sc.verts + 3 * ix4.x, *p1 = sc.verts + 3 * ix4.y, *p2 = sc.verts + 3 * ix4.z;
             double v0x = p0[0], v0y = p0[1], v0z = p0[2];

@@ -802,6 +802,7 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     for (int c = 0; c < 3; ++c) { s.cache_bmin[c] = d->cache_bmin[c]; s.cache_bmax[c] = d->cache_bmax[c]; }
     s.cache_res = d->cache_res;
     s.n_tris = nt;
+    s.n_tri4 = n_order;
     s.n_nodes = n_knodes;
     s.bvh_depth = B.max_depth_seen;
     s.n_lights = d->nl;
@@ -1335,8 +1336,9 @@ static hpt_status read_status(hpt_ctx *ctx)
     if (bits) {
         CUDA_TRY(cudaMemset(&ctx->d_scr->status, 0, sizeof bits));
         for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l) CUDA_TRY(cudaMemset(&ctx->d_scr_x[l]->status, 0, sizeof bits));
-        return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
-                    (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
+        return fail(HPT_ERR_DEVICE, "kernel status 0x%x:%s%s%s%s", bits, (bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
+                    (bits & ST_BAD_JOB) ? " bad-job" : "", (bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "",
+                    (bits & ST_BOUNDS) ? " index-out-of-bounds" : "");
     }
     return HPT_OK;
 }
@@ -1697,10 +1699,11 @@ static void finish_request(hpt_ctx *ctx, const std::shared_ptr<Request> &r, doub
     r->done = true;
     r->t_done = now;
     if (r->status == HPT_OK && r->dev_bits) {
-        char m[160];
-        snprintf(m, sizeof m, "request %llu: kernel status 0x%x%s%s%s", (unsigned long long)r->id, r->dev_bits,
+        char m[192];
+        snprintf(m, sizeof m, "request %llu: kernel status 0x%x%s%s%s%s", (unsigned long long)r->id, r->dev_bits,
                  (r->dev_bits & ST_STACK_OVERFLOW) ? " traversal-stack-overflow" : "",
-                 (r->dev_bits & ST_BAD_JOB) ? " bad-job" : "", (r->dev_bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "");
+                 (r->dev_bits & ST_BAD_JOB) ? " bad-job" : "", (r->dev_bits & ST_FALLBACK_STACK) ? " fp64-stack-overflow" : "",
+                 (r->dev_bits & ST_BOUNDS) ? " index-out-of-bounds" : "");
         r->status = HPT_ERR_DEVICE;
         r->err = m;
     }

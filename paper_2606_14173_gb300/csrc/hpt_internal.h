@@ -27,7 +27,16 @@ constexpr int MAX_ITER = 66;       // trace/shade iterations of a wave: max_dept
 constexpr int TILE_W = 8, TILE_H = 4;
 
 // status bits written by the kernels
-enum : uint32_t { ST_STACK_OVERFLOW = 1u, ST_BAD_JOB = 2u, ST_FALLBACK_STACK = 4u };
+enum : uint32_t { ST_STACK_OVERFLOW = 1u, ST_BAD_JOB = 2u, ST_FALLBACK_STACK = 4u, ST_BOUNDS = 8u };
+
+// The checked build (-DHPT_CHECKED=1, a separate library for tests): device indices into the
+// path state, the queues, the BVH and the triangle arrays are checked before use; a failing
+// check sets ST_BOUNDS in the status word and the access is skipped.  In the product build the
+// checks compile to nothing.
+#ifndef HPT_CHECKED
+#define HPT_CHECKED 0
+#endif
+#define HPT_IN(i, n) (!HPT_CHECKED || (unsigned)(i) < (unsigned)(n))
 
 // A constant needed by the coherent chain in both arithmetics: the double value and
 // its double-float split (hi = rn(x), lo = rn(x - hi)).
@@ -75,6 +84,7 @@ struct DevScene {
     float cache_bmin[3], cache_bmax[3];
     int cache_res;
     int n_tris, n_nodes, n_lights, n_points;
+    int n_tri4;               // triangle records in leaf order (the non-degenerate triangles)
 };
 
 struct DevJob {

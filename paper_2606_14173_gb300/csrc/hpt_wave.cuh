@@ -270,9 +270,17 @@ __global__ void __launch_bounds__(TRACE_BLOCK, COH ? HPT_TRACE_MINB : HPT_TRACE_
         if (COH) { kind = 0; qi = idx; }
         else if (idx < ni) { kind = 1; qi = idx; }
         else { kind = 2; qi = idx - ni; }
+        if (!HPT_IN(qi, pb.capacity)) {
+            status |= ST_BOUNDS;
+            continue;
+        }
         const int e = pb.q[kind][par][qi];
         if (kind < 2 && (e & Q_FINALIZE)) continue;   // no ray: a path that only waits for its shadow ray, or none
         const int p = e;
+        if (!HPT_IN(p, wd.n_paths)) {
+            status |= ST_BOUNDS;
+            continue;
+        }
         const DevScene &sc = jt->jobs[wd.seg[seg_of_path(wd, p)].job].sc;
         const float4 o4 = pb.ray_o[p], d4 = pb.ray_d[p];
         const int skip = __float_as_int(d4.w);
@@ -511,10 +519,19 @@ __global__ void __launch_bounds__(SHADE_BLOCK, COH ? HPT_SHADE_MINB : HPT_SHADE_
     int *const qn[3] = {pb.q[0][nx], pb.q[1][nx], pb.q[2][nx]};
     int *qcn = scr->qcount[it + 1];
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned status = 0;
     for (int idx = blockIdx.x * SHADE_BLOCK + threadIdx.x; idx < total; idx += gridDim.x * SHADE_BLOCK) {
+        if (!HPT_IN(idx, pb.capacity)) {
+            status |= ST_BOUNDS;
+            break;
+        }
         const int e = pb.q[COH ? 0 : 1][par][idx];
         if (COH && (e & Q_FINALIZE)) continue;
         const int p = e & 0x7FFFFFFF;
+        if (!HPT_IN(p, wd.n_paths)) {
+            status |= ST_BOUNDS;
+            continue;
+        }
         const PathId id = path_id(jt, wd, p);
         const DevJob &J = *id.J;
         const DevScene &sc = J.sc;
@@ -524,6 +541,10 @@ __global__ void __launch_bounds__(SHADE_BLOCK, COH ? HPT_SHADE_MINB : HPT_SHADE_
         bool do_vertex = false;
         if constexpr (COH) {
             const int tri = __float_as_int(pb.hit[p].w);
+            if (tri >= 0 && !HPT_IN(tri, sc.n_tris)) {
+                status |= ST_BOUNDS;
+                continue;
+            }
             if (tri >= 0) {
                 R3<R> co, cd;
                 R opl;
@@ -669,6 +690,10 @@ __global__ void __launch_bounds__(SHADE_BLOCK, COH ? HPT_SHADE_MINB : HPT_SHADE_
             if (!(e & Q_FINALIZE)) {
                 const float4 h = pb.hit[p];
                 const int tri = __float_as_int(h.w);
+                if (tri >= 0 && !HPT_IN(tri, sc.n_tris)) {
+                    status |= ST_BOUNDS;
+                    continue;
+                }
                 if (tri >= 0) {
                     const float4 o4 = pb.ray_o[p], d4 = pb.ray_d[p];
                     st.vfl = (st.vfl & ~VF_V) | ((st.vfl & VF_V) + 1);
@@ -697,6 +722,7 @@ __global__ void __launch_bounds__(SHADE_BLOCK, COH ? HPT_SHADE_MINB : HPT_SHADE_
         }
     }
     if (STATS) flush_counters(cnt, scr);
+    if (HPT_CHECKED && status) atomicOr(&scr->status, status);
 }
 
 // ------------------------------------------------------------------------------- s6 - s9
@@ -786,6 +812,10 @@ __global__ void __launch_bounds__(ACCUM_BLOCK, HPT_ACCUM_MINB) k_accum(const Job
     for (int j = 0; j < KMAX; ++j) ar[j] = ai[j] = cr[j] = ci[j] = 0.0f;
     for (int s = 0; s < spp; ++s) {
         const int p = g.path_offset + s * g.item_count + il;
+        if (!HPT_IN(p, wd.n_paths)) {
+            atomicOr(&scr->status, ST_BOUNDS);
+            break;
+        }
         const float amp = pb.amp[p];
         if (amp == 0.0f) continue;
         const float ft = pb.fturn[p];

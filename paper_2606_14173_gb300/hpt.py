@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libhpt.so")
+# HPT_LIB selects another build of the library (the checked build in its tests)
+LIB_PATH = os.environ.get("HPT_LIB") or os.path.join(_PKG, "_lib", "libhpt.so")
 
 HPT_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "BUSY",
