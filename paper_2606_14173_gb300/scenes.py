@@ -565,6 +565,22 @@ def lit_receiver_scene(kind=LAMBERT, albedo=0.6, rough=0.3, z=5 * MM, Le=10.0) -
     return b.build()
 
 
+def multi_light_receiver_scene(kind=LAMBERT, albedo=0.6, rough=0.3, z=5 * MM) -> Scene:
+    """The lit receiver with three rectangular lights of different sizes, positions and
+    emission, all outside every pixel's cone and facing the receiver: light selection for NEE
+    and its MIS weight over more than one light."""
+    b = _Builder("lit-receiver-3-lights")
+    m = b.material(kind, albedo=(albedo,) * 3, rough=rough)
+    b.quad(np.array([-3 * MM, -3 * MM, z]), np.array([6 * MM, 0, 0]), np.array([0, 6 * MM, 0]), m, flip=True)
+    b.rect_light(np.array([2 * MM, -1 * MM, 2 * MM]), np.array([2 * MM, 0, 0]), np.array([0, 2 * MM, 0]),
+                 np.array([10.0, 10.0, 10.0]))
+    b.rect_light(np.array([-4 * MM, -2.5 * MM, 3 * MM]), np.array([1.5 * MM, 0, 0]), np.array([0, 1 * MM, 0]),
+                 np.array([30.0, 20.0, 5.0]))
+    b.rect_light(np.array([-1 * MM, 2 * MM, 1.5 * MM]), np.array([0.5 * MM, 0, 0]), np.array([0, 0.5 * MM, 0.5 * MM]),
+                 np.array([5.0, 40.0, 80.0]))
+    return b.build()
+
+
 def slab_scene(z0=3 * MM, thick=1 * MM, ze=8 * MM, ior=1.5) -> Scene:
     """A dielectric slab (parallel faces z0 and z0 + thick) in front of a uniform emitter at ze."""
     b = _Builder("dielectric-slab")

@@ -172,6 +172,19 @@ def test_dielectric_slab_and_furnace(ctx, oracle_mod):
         ctx.release_scene(sid)
 
 
+@pytest.mark.parametrize("kind", [S.LAMBERT, S.GGX])
+def test_three_lights(ctx, oracle_mod, kind):
+    """NEE light selection and its MIS weight over three lights of different sizes, tilts and
+    emission (the other scenes have one light), Lambertian and GGX receivers, depth 2."""
+    sc = S.multi_light_receiver_scene(kind, albedo=0.7, rough=0.4)
+    r = S.config0_render(W=64, H=48, spp=16, max_depth=2, K=2)
+    sid = ctx.upload_scene(sc)
+    ref = oracle_mod.Oracle(sc).trace_full(r)
+    for prec in PRECS:
+        assert_parity(gpu_trace(ctx, sid, r, prec), ref, f"three lights kind {kind} prec {prec}")
+    ctx.release_scene(sid)
+
+
 @pytest.mark.parametrize("W,H,spp,K", [(1, 1, 1, 1), (7, 3, 2, 8), (33, 5, 1, 3)])
 def test_tiny_and_ragged_sizes(ctx, cfg0, W, H, spp, K):
     sc, sid, orc = cfg0

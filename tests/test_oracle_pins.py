@@ -230,6 +230,30 @@ def test_nee_matches_polygon_irradiance(oracle_mod, depth):
     assert ratios.mean() == pytest.approx(1.0, abs=4 * ratios.std() / math.sqrt(len(ratios)))
 
 
+@pytest.mark.parametrize("depth", [1, 2])
+def test_nee_over_three_lights_matches_polygon_irradiance(oracle_mod, depth):
+    """Three lights of different sizes, tilts and emission: NEE picks one uniformly and weights it
+    by the light count (depth 2 adds BSDF sampling with MIS over all three); the estimate of
+    rho/pi * sum of the lights' irradiances E(P) must be unbiased."""
+    rho = 0.6
+    sc = S.multi_light_receiver_scene(S.LAMBERT, albedo=rho)
+    o = oracle_mod.Oracle(sc)
+    polys = []
+    for L in sc.lights.astype(np.float64):
+        polys.append(([L[0:3], L[0:3] + L[3:6], L[0:3] + L[3:6] + L[6:9], L[0:3] + L[6:9]], L[9 + 1]))
+    r = S.config0_render(W=32, H=32, max_depth=depth, spp=1, phase_mode=S.PHASE_ZERO)
+    ratios = []
+    for pix in range(0, 1024, 3):
+        for s in range(24):
+            rec = o.sample(r, 0, pix, s)
+            assert rec["ok"]
+            P = np.array([rec["Px"], rec["Py"], rec["Pz"]])
+            E = sum(_polygon_irradiance(P, np.array([0, 0, -1.0]), poly, Le) for poly, Le in polys)
+            ratios.append(rec["L"] / (rho / math.pi * E))
+    ratios = np.array(ratios)
+    assert ratios.mean() == pytest.approx(1.0, abs=4 * ratios.std() / math.sqrt(len(ratios)))
+
+
 def test_ggx_nee_and_mis_agree(oracle_mod):
     """A GGX receiver: NEE alone (depth 1) and NEE + BSDF sampling with MIS (depth 2) are two
     estimators of the same integral and must agree in expectation."""
