@@ -305,9 +305,8 @@ __global__ void COLS_BOUNDS(LOGN, C) k_asm_cols(float2 *A, int Wp, int H, int oy
                                        // only the window's rows are loaded (a predicated load)
                                        return (y >= 0 && y < H) ? col[(size_t)y * Wp] : make_float2(0.0f, 0.0f);
                                    },
-                                   [&](int i, float2 v) { buf[spad(i)] = v; }, t);
-    for (int i = t; i < (1 << LOGN); i += fft_threads(1 << LOGN)) buf[spad(i)] = cmul(buf[spad(i)], __ldg(h + i));
-    __syncthreads();
+                                   // the transfer function applied as the last pass stores the spectrum
+                                   [&](int i, float2 v) { buf[spad(i)] = cmul(v, __ldg(h + i)); }, t);
     row_fft<LOGN, +1, true, false>(tw, buf, [&](int i) { return buf[spad(i)]; },
                                    [&](int i, float2 v) {
                                        const int y = i - oy;
