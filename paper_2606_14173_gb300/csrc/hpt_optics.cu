@@ -299,15 +299,20 @@ __global__ void COLS_BOUNDS(LOGN, C) k_asm_cols(float2 *A, int Wp, int H, int oy
     float2 *col = A + (size_t)f * H * Wp + fx;           // row y at col[y * Wp]
     float2 *buf = sm + c * col_stride(1 << LOGN, C);
     const float2 *h = Ht + ((size_t)fx << LOGN);
+    constexpr int HSH = LOGN > 4 ? LOGN - 4 : 0;
+    auto HALF = [](int i) { return ((i >> HSH) & 1) != 0; };
     row_fft<LOGN, -1, false, true>(tw, buf,
                                    [&](int i) {
                                        const int y = i - oy;
                                        // only the window's rows are loaded (a predicated load)
                                        return (y >= 0 && y < H) ? col[(size_t)y * Wp] : make_float2(0.0f, 0.0f);
                                    },
-                                   // the transfer function applied as the last pass stores the spectrum
-                                   [&](int i, float2 v) { buf[spad(i)] = cmul(v, __ldg(h + i)); }, t);
-    row_fft<LOGN, +1, true, false>(tw, buf, [&](int i) { return buf[spad(i)]; },
+                                   // the transfer function, half of it applied as the forward
+                                   // transform's last pass stores the spectrum ...
+                                   [&](int i, float2 v) { buf[spad(i)] = HALF(i) ? v : cmul(v, __ldg(h + i)); }, t);
+    // ... the other half as the inverse transform's first pass loads it (each point once; a
+    // thread holds half as many transfer-function values at a time)
+    row_fft<LOGN, +1, true, false>(tw, buf, [&](int i) { return HALF(i) ? cmul(buf[spad(i)], __ldg(h + i)) : buf[spad(i)]; },
                                    [&](int i, float2 v) {
                                        const int y = i - oy;
                                        if (y >= 0 && y < H) col[(size_t)y * Wp] = v;
