@@ -378,18 +378,22 @@ cudaError_t with_logn(int logn, F f)
 }
 
 // exp(i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2)) on the padded grid (FFT order), times 'scale',
-// stored transposed: Ht[ix][iy]
+// stored transposed: Ht[ix][iy].  The value depends on fx^2 and fy^2 only, and the frequencies of
+// ix and Wp - ix (iy and Hp - iy) are exact negatives of each other, so each value is computed
+// once for ix <= Wp / 2, iy <= Hp / 2 (one block row per ix: grid Wp / 2 + 1 high) and stored
+// at its up to four mirror positions.
 __global__ void k_transfer(float2 *Hf, int Wp, int Hp, float2 fx_unit, float2 fy_unit, float2 inv_lambda2, float2 zdist,
                            float scale)
 {
     // double-float arithmetic (~48-bit significands): the phase runs to ~1e5 turns and its
     // fraction must hold ~1e-7
-    const int ix = blockIdx.y;                               // one transposed row per fx
+    const int ix = blockIdx.y;                               // 0 .. Wp / 2
     const df fx = mul_f(mkdf(fx_unit.x, fx_unit.y), (float)(ix < Wp / 2 ? ix : ix - Wp));
     const df base = mkdf(inv_lambda2.x, inv_lambda2.y) - fx * fx;
     const df fyu = mkdf(fy_unit.x, fy_unit.y), z = mkdf(zdist.x, zdist.y);
     float2 *row = Hf + (size_t)ix * Hp;
-    for (int iy = blockIdx.x * blockDim.x + threadIdx.x; iy < Hp; iy += gridDim.x * blockDim.x) {
+    float2 *row2 = (ix > 0 && ix < Wp / 2) ? Hf + (size_t)(Wp - ix) * Hp : nullptr;
+    for (int iy = blockIdx.x * blockDim.x + threadIdx.x; iy <= Hp / 2; iy += gridDim.x * blockDim.x) {
         const df fy = mul_f(fyu, (float)(iy < Hp / 2 ? iy : iy - Hp));
         const df a = base - fy * fy;
         float2 v = make_float2(0.0f, 0.0f);
@@ -399,9 +403,18 @@ __global__ void k_transfer(float2 *Hf, int Wp, int Hp, float2 fx_unit, float2 fy
             sincospif(2.0f * f, &sn, &cs);
             v = make_float2(cs * scale, sn * scale);
         }
+        const bool my = iy > 0 && iy < Hp / 2;
         row[iy] = v;
+        if (my) row[Hp - iy] = v;
+        if (row2) {
+            row2[iy] = v;
+            if (my) row2[Hp - iy] = v;
+        }
     }
 }
+
+// the launch shape of k_transfer for a Wp x Hp grid
+inline dim3 transfer_grid(int Wp, int Hp) { return dim3((Hp / 2 + 1 + 255) / 256, Wp / 2 + 1); }
 
 // a double as a double-float pair (head, tail)
 float2 to_df(double x)
@@ -728,7 +741,7 @@ extern "C" hpt_status hpt_asm_propagate(hpt_ctx *ctx, const void *in_dev, void *
     k_twiddles<<<(Wp + 255) / 256, 256, 0, s>>>(P.twx, Wp);
     k_twiddles<<<(Hp + 255) / 256, 256, 0, s>>>(P.twy, Hp);
     for (int l = 0; l < n_lambda; ++l)
-        k_transfer<<<dim3((Hp + 255) / 256, Wp), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, to_df(1.0 / (Wp * pitch)),
+        k_transfer<<<transfer_grid(Wp, Hp), 256, 0, s>>>(Hf + (size_t)l * np, Wp, Hp, to_df(1.0 / (Wp * pitch)),
                                                               to_df(1.0 / (Hp * pitch)),
                                                               to_df(1.0 / (lambdas[l] * lambdas[l])), to_df(z),
                                                               1.0f / (float)np);
@@ -775,7 +788,7 @@ extern "C" hpt_status hpt_phase_encode(hpt_ctx *ctx, const void *target_dev, flo
     const float2 *T = (const float2 *)target_dev;
     k_twiddles<<<(P.Wp + 255) / 256, 256, 0, s>>>(P.twx, P.Wp);
     k_twiddles<<<(P.Hp + 255) / 256, 256, 0, s>>>(P.twy, P.Hp);
-    const dim3 tg((P.Hp + 255) / 256, P.Wp);
+    const dim3 tg = transfer_grid(P.Wp, P.Hp);
     const float2 fxu = to_df(1.0 / (P.Wp * pitch)), fyu = to_df(1.0 / (P.Hp * pitch)), il2 = to_df(1.0 / (lambda * lambda));
     k_transfer<<<tg, 256, 0, s>>>(Hp_, P.Wp, P.Hp, fxu, fyu, il2, to_df(z), 1.0f / (float)np);
     k_transfer<<<tg, 256, 0, s>>>(Hm, P.Wp, P.Hp, fxu, fyu, il2, to_df(-z), 1.0f / (float)np);
