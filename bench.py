@@ -565,7 +565,8 @@ def main():
         h2d = ctypes.sizeof(hpt.RenderDesc)   # the render descriptor, copied to the device per call
         e2e = {"value": world * samples_per_step * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(host.nbytes),
-               "api": "hpt_trace_host (device trace + D2H copy of all K x 3 fields into pinned host memory)"}
+               "api": "hpt_trace_host (device trace; the rows each wave completes copied into pinned host memory "
+                      "while later waves run, all K x 3 fields per step)"}
 
     # roofline of the dominant kernel (k_trace): its algorithmic FP32 work per frame from the work
     # counters, over its own device time per frame from CUDA events around every launch

@@ -194,7 +194,11 @@ hpt_status hpt_scene_info(hpt_ctx *ctx, uint64_t scene_id, uint64_t *device_byte
 hpt_status hpt_trace(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                      void *out_dev, size_t out_bytes, void *cuda_stream);
 /* Same, end to end with host memory: the result is copied into out_host (pinned or pageable)
- * before the call returns.  Uses a device buffer owned by the context. */
+ * before the call returns.  Uses a device buffer owned by the context.  Into pinned memory
+ * (cudaHostAlloc / cudaHostRegister) the rows of the fields are copied as the waves that
+ * complete them finish, on a stream of the context, overlapping the rest of the trace (the
+ * frame then runs without a captured graph); into pageable memory the whole frame runs first
+ * and one copy follows.  The fields are the same either way. */
 hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_render_desc *desc,
                           void *out_host, size_t out_bytes, void *cuda_stream);
 /* Block until all work queued by this context has finished; then report (and clear) the

@@ -330,6 +330,10 @@ struct hpt_ctx {
     Slot slots[NSLOTS];
     int next_slot = 0;
     void *host_out_dev = nullptr;
+    // hpt_trace_host into pinned memory: finished rows leave on their own stream while later
+    // waves run
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_wave = nullptr, ev_copied = nullptr;
     float4 *d_sincos = nullptr;
     size_t host_out_bytes = 0;
     std::chrono::steady_clock::time_point t0;
@@ -497,6 +501,9 @@ extern "C" void hpt_destroy(hpt_ctx *ctx)
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+    if (ctx->ev_wave) cudaEventDestroy(ctx->ev_wave);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
     if (ctx->d_sincos) cudaFree(ctx->d_sincos);
     delete ctx;
 }
@@ -1037,11 +1044,13 @@ static hpt_status ensure_sched_paths(hpt_ctx *ctx)
     return HPT_OK;
 }
 
-// One launch group: the waves covering all items of 'jobs', queued on the context's wave
-// stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
+// Called after each wave's accumulation is queued, with the wave and the stream it ran on.
+using AfterWave = std::function<hpt_status(const WaveDesc &, cudaStream_t)>;
+
 // Queue the waves that cover all items of 'jobs' (job table already on the device) on ws.
+// Waves take the items of each job in increasing order.  Caller holds ctx->mu.
 static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, const JobTable *jt,
-                                cudaStream_t ws, bool allow_debug)
+                                cudaStream_t ws, bool allow_debug, const AfterWave *after_wave = nullptr)
 {
     const int B = ctx->capacity;
     WaveDesc wd;
@@ -1086,6 +1095,10 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
         CUDA_TRY(mark(HPT_K_ACCUM));
         CUDA_TRY(wave_accum(prec, jt, wd, pb, scr, s));
         CUDA_TRY(mark(-1));
+        if (after_wave) {
+            hpt_status st2 = (*after_wave)(wd, s);
+            if (st2) return st2;
+        }
         if (allow_debug && ctx->debug_waves > 0) {
             // diagnostic: queue lengths per iteration of the first waves (HPT_DEBUG_WAVES=n)
             --ctx->debug_waves;
@@ -1143,7 +1156,8 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
 
 // One launch group: the waves covering all items of 'jobs', queued on the context's wave
 // stream after the caller's stream, which then waits for them.  Caller holds ctx->mu.
-static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t user)
+static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bool stats, cudaStream_t user,
+                           const AfterWave *after_wave = nullptr)
 {
     hpt_status st = ensure_paths(ctx);
     if (st) return st;
@@ -1161,7 +1175,7 @@ static hpt_status run_jobs(hpt_ctx *ctx, const DevJob *jobs, int n, int prec, bo
         for (int l = 0; l < hpt_ctx::EXTRA_LANES; ++l)
             CUDA_TRY(cudaMemsetAsync(ctx->d_scr_x[l]->counters, 0, sizeof(ctx->d_scr->counters), ws));
     }
-    st = enqueue_waves(ctx, jobs, n, prec, stats, slot->d_table, ws, true);
+    st = enqueue_waves(ctx, jobs, n, prec, stats, slot->d_table, ws, true, after_wave);
     if (st) return st;
     CUDA_TRY(cudaEventRecord(slot->done, ws));
     CUDA_TRY(cudaEventRecord(ctx->ev_out, ws));
@@ -1310,11 +1324,62 @@ extern "C" hpt_status hpt_trace_host(hpt_ctx *ctx, uint64_t scene_id, const hpt_
         Range() { nvtxRangePushA("hpt_trace_host frame + copy"); }
         ~Range() { nvtxRangePop(); }
     } range;
-    // the device staging buffer is the context's, so the frame's captured graph is reused
-    st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, s)
-                                                  : run_jobs(ctx, &J, 1, desc->precision, false, s);
-    if (st) return st;
-    CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out_dev, need, cudaMemcpyDeviceToHost, s));
+    cudaPointerAttributes pa{};
+    const bool pinned = cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    if (!pinned) (void)cudaGetLastError();   // an unregistered pointer is not an error here
+    if (!pinned || ctx->debug_waves > 0) {
+        // pageable memory: a copy into it would hold the host until it ends, so the whole frame
+        // runs first (the staging buffer is the context's, so its captured graph is reused)
+        st = ctx->use_graphs && ctx->debug_waves == 0 ? run_graph(ctx, J, desc->precision, s)
+                                                      : run_jobs(ctx, &J, 1, desc->precision, false, s);
+        if (st) return st;
+        CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out_dev, need, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return HPT_OK;
+    }
+    // pinned memory: the fields' rows are final once every pixel of their tile row has been
+    // accumulated, and waves take the items (lambda-major, tile rows in order) in increasing
+    // order, so after each wave the rows it completed are copied on the copy stream, behind an
+    // event of that wave (the copy stream has waited for every earlier wave as well); only the
+    // last wave's rows are copied after the trace
+    if (!ctx->cstream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    if (!ctx->ev_wave) CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_wave, cudaEventDisableTiming));
+    if (!ctx->ev_copied) CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+    const long long per_lam = (long long)J.n_tiles * 32, row_items = (long long)J.n_tiles_x * 32;
+    const int n_rows = J.n_tiles / J.n_tiles_x;   // tile rows of one wavelength
+    long long copied = 0;                         // tile rows (lambda * n_rows + row) copied so far
+    char *dst = (char *)out_host;
+    const char *src = (const char *)ctx->host_out_dev;
+    const AfterWave after = [&](const WaveDesc &wd, cudaStream_t ls) -> hpt_status {
+        long long end = 0;
+        for (int i = 0; i < wd.n_seg; ++i) end = std::max(end, wd.seg[i].item_begin + wd.seg[i].item_count);
+        CUDA_TRY(cudaEventRecord(ctx->ev_wave, ls));
+        CUDA_TRY(cudaStreamWaitEvent(ctx->cstream, ctx->ev_wave, 0));
+        const long long done = (end / per_lam) * n_rows + (end % per_lam) / row_items;
+        while (copied < done) {
+            const int lam = (int)(copied / n_rows), r0 = (int)(copied % n_rows);
+            const int r1 = (int)std::min<long long>(n_rows, r0 + (done - copied));
+            const int y0 = r0 * TILE_H, y1 = std::min(r1 * TILE_H, J.H);
+            for (int k = 0; k < J.K; ++k) {
+                const size_t off = (((size_t)lam * J.K + k) * J.H + y0) * J.W * sizeof(float2);
+                CUDA_TRY(cudaMemcpyAsync(dst + off, src + off, (size_t)(y1 - y0) * J.W * sizeof(float2),
+                                         cudaMemcpyDeviceToHost, ctx->cstream));
+            }
+            copied += r1 - r0;
+        }
+        return HPT_OK;
+    };
+    st = run_jobs(ctx, &J, 1, desc->precision, false, s, &after);
+    if (st) {
+        cudaStreamSynchronize(ctx->cstream);   // no copy lands in out_host after the call returns
+        return st;
+    }
+    if (copied != (long long)desc->n_lambda * n_rows) {
+        cudaStreamSynchronize(ctx->cstream);
+        return fail(HPT_ERR_CUDA, "copy-out covered %lld of %lld tile rows", copied, (long long)desc->n_lambda * n_rows);
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev_copied, ctx->cstream));
+    CUDA_TRY(cudaStreamWaitEvent(s, ctx->ev_copied, 0));
     CUDA_TRY(cudaStreamSynchronize(s));
     return HPT_OK;
 }

@@ -63,6 +63,47 @@ def test_trace_into_host_memory_equals_device_trace(torch_cuda):
             ctx.close()
 
 
+def _ctx_with_wave_paths(n, **kw):
+    import os
+    from paper_2606_14173_gb300 import hpt
+    old = os.environ.get("HPT_WAVE_PATHS")
+    os.environ["HPT_WAVE_PATHS"] = str(n)
+    try:
+        return hpt.Context(0, **kw)
+    finally:
+        if old is None:
+            del os.environ["HPT_WAVE_PATHS"]
+        else:
+            os.environ["HPT_WAVE_PATHS"] = old
+
+
+def test_trace_into_pinned_host_memory_row_by_row(torch_cuda):
+    """hpt_trace_host into pinned memory copies the rows each wave completes while later waves
+    run.  Small waves whose item ranges end inside tiles and inside tile rows (spp 7 and 3), tile
+    rows longer than a wave (a row finished only by the next wave), three wavelengths and sizes
+    that are not multiples of the 8x4 tile: the host fields equal the device trace's bit for bit,
+    every element written (the buffer starts as NaN), with and without captured graphs for the
+    device trace, and after a larger request grows the staging buffer."""
+    torch = torch_cuda
+    from paper_2606_14173_gb300 import hpt
+    sc = S.config1_scene()
+    for paths, cases in ((65536, ((203, 117, 4, 7, 1), (320, 180, 8, 8, 2), (203, 117, 4, 7, 3))),
+                         (4096, ((643, 21, 2, 3, 4), (203, 117, 1, 5, 5)))):
+        for graphs in (True, False):
+            ctx = _ctx_with_wave_paths(paths, graphs=graphs)
+            try:
+                sid = ctx.upload_scene(sc)
+                for W, H, K, spp, seed in cases:
+                    r = S.config1_render(W=W, H=H, spp=spp, K=K, seed=seed, max_depth=2)
+                    ref = _trace(ctx, sid, r, hpt.alloc_output(r))
+                    host = torch.empty(ref.shape, dtype=torch.complex64, pin_memory=True).numpy()
+                    host[...] = np.nan
+                    ctx.trace_host(sid, r, host)
+                    assert np.array_equal(host, ref), (paths, graphs, W, H, K, spp, seed)
+            finally:
+                ctx.close()
+
+
 def test_autotune_keeps_results(torch_cuda):
     from paper_2606_14173_gb300 import hpt
     ctx = hpt.Context(0)
