@@ -164,6 +164,8 @@ def test_mirror_and_transform_cases(ctx, oracle_mod, prec):
 
 def test_dielectric_slab_and_furnace(ctx, oracle_mod):
     for sc, r in ((S.slab_scene(), S.config0_render(W=40, H=40, spp=16, max_depth=3)),
+                  # an emitter inside the slab: one refraction, throughput 1/n^2
+                  (S.slab_scene(ze=3.8e-3, thick=2e-3), S.config0_render(W=40, H=40, spp=16, max_depth=3)),
                   (S.furnace_scene(), S.config0_render(W=32, H=32, spp=4, max_depth=3)),
                   (S.lit_receiver_scene(S.GGX, albedo=0.8, rough=0.4), S.config0_render(W=48, H=32, spp=8, max_depth=2))):
         sid = ctx.upload_scene(sc)

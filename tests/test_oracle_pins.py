@@ -306,6 +306,34 @@ def test_slab_refraction_opl_closed_form(oracle_mod):
     assert checked > 2000
 
 
+def test_emitter_inside_a_dielectric_closed_form(oracle_mod):
+    """An emitter inside a dielectric slab seen through its front face: one refraction into the
+    medium, so the path throughput is (n_i/n_t)^2 = 1/n^2 (radiance emitted in the medium loses
+    n^2 on the way out into air) and d_OPL = z0/cos(theta) + n (ze - z0)/cos(theta_t).  Fixes the
+    direction of the radiance scaling, which the slab's in-and-out case leaves open."""
+    z0, thick, n = 3e-3, 2e-3, 1.5
+    sc = S.slab_scene(z0=z0, thick=thick, ze=z0 + 0.8e-3, ior=n)
+    o = oracle_mod.Oracle(sc)
+    zs = sorted(set(float(v) for v in sc.verts[:, 2]))     # front face, emitter, back face (float32)
+    z0, ze = zs[0], zs[1]
+    n = float(np.float32(n))
+    r = S.config0_render(W=16, H=16, spp=64, max_depth=3, phase_mode=S.PHASE_ZERO)
+    checked = 0
+    for pix in range(0, 256, 5):
+        for s in range(64):
+            rec = o.sample(r, 0, pix, s)
+            if not rec["ok"] or rec["vP"] != 2:
+                continue
+            ct = rec["cos"]
+            st = math.sqrt(1 - ct * ct)
+            ctt = math.sqrt(1 - (st / n) ** 2)
+            assert rec["opl"] == pytest.approx(z0 / ct + n * (ze - z0) / ctt, rel=1e-13)
+            assert rec["beta"] == pytest.approx(1.0 / n ** 2, rel=1e-13)
+            assert rec["L"] == pytest.approx(1.0, rel=1e-13)   # Le of the emitter, albedo 0
+            checked += 1
+    assert checked > 2000
+
+
 def test_path_reuse_hologram_index_invariance(oracle_mod):
     """Sec. 4.3: only the facet phase depends on m; hologram m of a K = 8 run equals a K = 1 run
     offset to m, and zero phase makes all holograms equal."""
