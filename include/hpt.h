@@ -176,11 +176,14 @@ void hpt_destroy(hpt_ctx *ctx);
 /* Message of the last failing call on this thread ("" if none). Valid until the next call. */
 const char *hpt_last_error(void);
 
-/* Copy a scene to the device, build its BVH; *scene_id receives a handle. Synchronous. */
+/* Copy a scene to the device and build its BVHs (binned SAH over the triangles; a second tree
+ * of the same triangles, its SAH weighting the box faces across the hologram plane's z axis, is
+ * walked by the pixels' first rays); *scene_id receives a handle. Synchronous. */
 hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *scene, uint64_t *scene_id);
 /* Free a scene after all work using it has finished. */
 hpt_status hpt_scene_release(hpt_ctx *ctx, uint64_t scene_id);
-/* Bytes of device memory the scene occupies (BVH, triangles, attributes, textures, cache). */
+/* Bytes of device memory the scene occupies (both BVHs, triangles, attributes, textures, cache);
+ * n_nodes and bvh_depth describe the tree of the rays in every direction. */
 hpt_status hpt_scene_info(hpt_ctx *ctx, uint64_t scene_id, uint64_t *device_bytes,
                           int32_t *n_nodes, int32_t *bvh_depth);
 

@@ -137,7 +137,7 @@ __device__ __forceinline__ void ldg256(const float4 *p, float4 &a, float4 &b)
 template <bool STATS, int SSTRIDE>
 __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d, float tmax, int skip, float eps_w,
                                          bool TRACK, bool ANYHIT, HitF &h, Cands &cand, int *stk, int slimit,
-                                         int &status, Counters &cnt)
+                                         int &status, Counters &cnt, bool primary = false)
 {
     const float big = 1e30f;
     float3 inv = f3(fabsf(d.x) > 1e-20f ? 1.0f / d.x : copysignf(1e20f, d.x),
@@ -150,8 +150,13 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     (void)big;
     if (TRACK) cand.n = 0;
     const float cull = TRACK ? (1.0f + 4.0f * TIE_REL) : 1.0f;
-    const float4 *__restrict__ nodes = sc.nodes;
-    const float4 *__restrict__ tris = sc.tri4;
+    // the pixels' first rays walk the tree built for their direction; the closest hit and the
+    // candidates do not depend on the tree
+    const float4 *__restrict__ nodes = primary ? sc.nodes_p : sc.nodes;
+    const float4 *__restrict__ tris = primary ? sc.tri4_p : sc.tri4;
+    const int n_nodes = primary ? sc.n_nodes_p : sc.n_nodes, n_tri4 = primary ? sc.n_tri4_p : sc.n_tri4;
+    (void)n_nodes;
+    (void)n_tri4;
     int sp = 0;
     int node = 0;
     // Speculative descent (Aila and Laine 2009): a leaf met while none is pending is postponed
@@ -163,7 +168,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
     int LEAF = 0;                   // pending leaf (< 0); 0 = none (the root is never a leaf)
     for (;;) {
         while (node >= 0 && node != SENT) {
-            if (!HPT_IN(node, sc.n_nodes)) {
+            if (!HPT_IN(node, n_nodes)) {
                 status |= ST_BOUNDS;
                 node = SENT;
                 break;
@@ -207,7 +212,7 @@ __device__ __forceinline__ bool traverse(const DevScene &sc, float3 o, float3 d,
             // leaf: ~(start << 8 | count)
             int code = ~LEAF;
             int start = code >> 8, count = code & 255;
-            if (count > 0 && !HPT_IN(start + count - 1, sc.n_tri4)) {
+            if (count > 0 && !HPT_IN(start + count - 1, n_tri4)) {
                 status |= ST_BOUNDS;
                 count = 0;
             }

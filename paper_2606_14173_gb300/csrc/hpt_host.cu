@@ -88,12 +88,6 @@ struct Box {
     {
         for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
     }
-    double area() const
-    {
-        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
-        if (dx < 0 || dy < 0 || dz < 0) return 0.0;
-        return 2.0 * (dx * dy + dy * dz + dz * dx);
-    }
 };
 
 struct BuildNode {
@@ -118,15 +112,29 @@ struct Builder {
 #ifndef HPT_LEAF_CAP
 #define HPT_LEAF_CAP 4
 #endif
+#ifndef HPT_PRIMARY_SIDE_W
+#define HPT_PRIMARY_SIDE_W 0.2
+#endif
     // SAH in units of one triangle test: a split costs CT (one node visit) times the node's area
     // plus the children's area-weighted triangle counts; a leaf costs its area times its count.
     // Nodes of at most LEAF_MAX triangles are always leaves, nodes of up to LEAF_CAP become
     // leaves when no split is cheaper.
     static constexpr int BINS = 32, LEAF_MAX = HPT_LEAF_MAX, LEAF_CAP = HPT_LEAF_CAP, DEPTH_LIMIT = TSTACK - 1;
     static constexpr double CT = HPT_SAH_CT;
+    // weights of the box faces normal to x, y and z in the surface-area heuristic: all 1 for
+    // rays in every direction; rays along one axis meet a box in proportion to its face across
+    // that axis, so a tree for them weights the other two faces down
+    double wface[3] = {1.0, 1.0, 1.0};
 
     Builder(const std::vector<Box> &pb_, const std::vector<float> &c_, std::vector<int> prims)
         : pb(pb_), cent(c_), idx(std::move(prims)) {}
+
+    double area(const Box &b) const
+    {
+        double dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+        if (dx < 0 || dy < 0 || dz < 0) return 0.0;
+        return 2.0 * (wface[0] * dy * dz + wface[1] * dz * dx + wface[2] * dx * dy);
+    }
 
     int make_leaf(const Box &b, int start, int count)
     {
@@ -172,7 +180,7 @@ struct Builder {
             for (int k = 0; k < BINS - 1; ++k) {
                 acc.grow(bb[k]);
                 n += bc[k];
-                la[k] = acc.area();
+                la[k] = area(acc);
                 ln[k] = n;
             }
             acc.reset();
@@ -181,11 +189,11 @@ struct Builder {
                 acc.grow(bb[k]);
                 n += bc[k];
                 if (ln[k - 1] == 0 || n == 0) continue;
-                double cost = CT * b.area() + la[k - 1] * ln[k - 1] + acc.area() * n;
+                double cost = CT * area(b) + la[k - 1] * ln[k - 1] + area(acc) * n;
                 if (cost < best_cost) { best_cost = cost; best_axis = ax; best_split = k; }
             }
         }
-        double leaf_cost = b.area() * count;
+        double leaf_cost = area(b) * count;
         if (depth < DEPTH_LIMIT && count <= 255 && (best_axis < 0 || (best_cost >= leaf_cost && count <= LEAF_CAP)))
             return make_leaf(b, start, count);
         if (depth >= DEPTH_LIMIT) best_axis = -1;   // forced median split of an oversized deep node
@@ -573,122 +581,143 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
         if (n0 * n0 + n1 * n1 + n2 * n2 > 0.0) prims.push_back(t);
     }
     if (prims.empty()) return fail(HPT_ERR_INVALID_ARG, "all triangles are degenerate");
-    Builder B(pb, cent, prims);
-    int root = B.build(0, (int)B.idx.size(), 0);
-    // flatten: kernel nodes hold both child boxes; leaves are encoded in the parent's link
+    // a tree: kernel nodes (both child boxes of an inner node; leaves encoded in the parent's
+    // link) and the triangle records in its leaf order
+    struct Tree {
+        std::vector<float4> knodes, tri4;
+        int n_nodes = 0, n_tri4 = 0, depth = 0;
+    };
     const float pad = 2e-6f * max_abs + 1e-12f;
-    std::vector<float4> knodes;
-    std::vector<int> order;   // triangle ids in leaf order
-    order.reserve(B.idx.size());
-    auto emit_leaf_link = [&](const BuildNode &n) {
-        int start = (int)order.size();
-        for (int i = n.start; i < n.start + n.count; ++i) order.push_back(B.idx[i]);
-        return ~((start << 8) | n.count);
-    };
-    auto box_of = [&](const BuildNode *n, float lo[3], float hi[3]) {
-        for (int k = 0; k < 3; ++k) {
-            if (n) {
-                lo[k] = n->box.lo[k] - pad;
-                hi[k] = n->box.hi[k] + pad;
-            } else {
-                lo[k] = 1e30f;   // far-away point box: no ray with t < 1e30 enters it
-                hi[k] = 1e30f;
-            }
-        }
-    };
-    // kernel nodes in depth-first order (a node's first child follows it in memory): the root
-    // is an inner node whose children are the build root's children (or the root leaf)
-    std::function<int(const BuildNode *, const BuildNode *)> emit = [&](const BuildNode *c0, const BuildNode *c1) -> int {
-        const int kn = (int)(knodes.size() / 4);
-        knodes.resize(knodes.size() + 4);
-        const BuildNode *c[2] = {c0, c1};
-        float lo[2][3], hi[2][3];
-        int link[2];
-        for (int s2 = 0; s2 < 2; ++s2) {
-            box_of(c[s2], lo[s2], hi[s2]);
-            if (!c[s2]) link[s2] = ~0;   // empty leaf, never entered
-            else if (c[s2]->count) link[s2] = emit_leaf_link(*c[s2]);
-            else link[s2] = emit(&B.nodes[c[s2]->left], &B.nodes[c[s2]->right]);
-        }
-        float4 *o = &knodes[4 * kn];
-        o[0] = make_float4(lo[0][0], hi[0][0], lo[0][1], hi[0][1]);
-        o[1] = make_float4(lo[1][0], hi[1][0], lo[1][1], hi[1][1]);
-        o[2] = make_float4(lo[0][2], hi[0][2], lo[1][2], hi[1][2]);
-        float l0, l1;
-        memcpy(&l0, &link[0], 4);
-        memcpy(&l1, &link[1], 4);
-        o[3] = make_float4(l0, l1, 0.0f, 0.0f);
-        return kn;
-    };
-    {
-        const BuildNode &r = B.nodes[root];
-        if (r.count) emit(&r, nullptr);
-        else emit(&B.nodes[r.left], &B.nodes[r.right]);
-    }
-    const int n_knodes = (int)(knodes.size() / 4);
-    const int n_order = (int)order.size();
-    {
-        // the first TOP_ORDER inner nodes breadth-first from the root, the others in their
-        // depth-first order; the links are renumbered (the tree itself is unchanged)
-        const int ntop = std::min(n_knodes, TOP_ORDER);
-        std::vector<int> bfs;
-        std::vector<char> top(n_knodes, 0);
-        bfs.reserve(ntop);
-        bfs.push_back(0);
-        top[0] = 1;
-        for (size_t h = 0; h < bfs.size() && (int)bfs.size() < ntop; ++h) {
-            int link[2];
-            memcpy(&link[0], &knodes[4 * (size_t)bfs[h] + 3].x, 4);
-            memcpy(&link[1], &knodes[4 * (size_t)bfs[h] + 3].y, 4);
-            for (int c = 0; c < 2; ++c)
-                if (link[c] >= 0 && (int)bfs.size() < ntop) {
-                    bfs.push_back(link[c]);
-                    top[link[c]] = 1;
+    auto make_tree = [&](const double wface[3], Tree &T) {
+        Builder B(pb, cent, prims);
+        for (int k = 0; k < 3; ++k) B.wface[k] = wface[k];
+        int root = B.build(0, (int)B.idx.size(), 0);
+        std::vector<float4> &knodes = T.knodes;
+        std::vector<int> order;   // triangle ids in leaf order
+        order.reserve(B.idx.size());
+        auto emit_leaf_link = [&](const BuildNode &n) {
+            int start = (int)order.size();
+            for (int i = n.start; i < n.start + n.count; ++i) order.push_back(B.idx[i]);
+            return ~((start << 8) | n.count);
+        };
+        auto box_of = [&](const BuildNode *n, float lo[3], float hi[3]) {
+            for (int k = 0; k < 3; ++k) {
+                if (n) {
+                    lo[k] = n->box.lo[k] - pad;
+                    hi[k] = n->box.hi[k] + pad;
+                } else {
+                    lo[k] = 1e30f;   // far-away point box: no ray with t < 1e30 enters it
+                    hi[k] = 1e30f;
                 }
-        }
-        std::vector<int> nid(n_knodes);
-        int k = 0;
-        for (int n : bfs) nid[n] = k++;
-        for (int n = 0; n < n_knodes; ++n)
-            if (!top[n]) nid[n] = k++;
-        std::vector<float4> re(knodes.size());
-        for (int n = 0; n < n_knodes; ++n) {
-            float4 *o = &re[4 * (size_t)nid[n]];
-            for (int j = 0; j < 4; ++j) o[j] = knodes[4 * (size_t)n + j];
+            }
+        };
+        // kernel nodes in depth-first order (a node's first child follows it in memory): the
+        // root is an inner node whose children are the build root's children (or the root leaf)
+        std::function<int(const BuildNode *, const BuildNode *)> emit = [&](const BuildNode *c0,
+                                                                            const BuildNode *c1) -> int {
+            const int kn = (int)(knodes.size() / 4);
+            knodes.resize(knodes.size() + 4);
+            const BuildNode *c[2] = {c0, c1};
+            float lo[2][3], hi[2][3];
             int link[2];
-            memcpy(&link[0], &o[3].x, 4);
-            memcpy(&link[1], &o[3].y, 4);
-            for (int c = 0; c < 2; ++c)
-                if (link[c] >= 0) link[c] = nid[link[c]];
-            memcpy(&o[3].x, &link[0], 4);
-            memcpy(&o[3].y, &link[1], 4);
+            for (int s2 = 0; s2 < 2; ++s2) {
+                box_of(c[s2], lo[s2], hi[s2]);
+                if (!c[s2]) link[s2] = ~0;   // empty leaf, never entered
+                else if (c[s2]->count) link[s2] = emit_leaf_link(*c[s2]);
+                else link[s2] = emit(&B.nodes[c[s2]->left], &B.nodes[c[s2]->right]);
+            }
+            float4 *o = &knodes[4 * kn];
+            o[0] = make_float4(lo[0][0], hi[0][0], lo[0][1], hi[0][1]);
+            o[1] = make_float4(lo[1][0], hi[1][0], lo[1][1], hi[1][1]);
+            o[2] = make_float4(lo[0][2], hi[0][2], lo[1][2], hi[1][2]);
+            float l0, l1;
+            memcpy(&l0, &link[0], 4);
+            memcpy(&l1, &link[1], 4);
+            o[3] = make_float4(l0, l1, 0.0f, 0.0f);
+            return kn;
+        };
+        {
+            const BuildNode &r = B.nodes[root];
+            if (r.count) emit(&r, nullptr);
+            else emit(&B.nodes[r.left], &B.nodes[r.right]);
         }
-        knodes.swap(re);
-    }
-
-    // triangle records
-    std::vector<float4> tri4(3 * (size_t)std::max(n_order, 1));
-    for (int i = 0; i < n_order; ++i) {
-        int t = order[i];
-        const float *p0 = d->verts + 3 * d->tris[3 * t], *p1 = d->verts + 3 * d->tris[3 * t + 1],
-                    *p2 = d->verts + 3 * d->tris[3 * t + 2];
-        float idf;
-        memcpy(&idf, &t, 4);
-        // barycentric slack of the float test on incoherent rays: a band of 1e-6 x the scene's
-        // largest coordinate (a few float ulps of a hit point) across the triangle's shortest
-        // altitude, at most 2e-5
-        double a[3] = {(double)p1[0] - p0[0], (double)p1[1] - p0[1], (double)p1[2] - p0[2]};
-        double b[3] = {(double)p2[0] - p0[0], (double)p2[1] - p0[1], (double)p2[2] - p0[2]};
-        double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-        double area2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-        double c3[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-        double lmax = sqrt(std::max({a[0] * a[0] + a[1] * a[1] + a[2] * a[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2],
-                                     c3[0] * c3[0] + c3[1] * c3[1] + c3[2] * c3[2]}));
-        double hmin = lmax > 0.0 ? area2 / lmax : 0.0;
-        float slack = hmin > 0.0 ? (float)std::min(2e-5, 1e-6 * (double)max_abs / hmin) : 2e-5f;
-        tri4[3 * i] = make_float4(p0[0], p0[1], p0[2], idf);
-        tri4[3 * i + 1] = make_float4(p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2], slack);
-        tri4[3 * i + 2] = make_float4(p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2], 0.0f);
+        const int n_knodes = (int)(knodes.size() / 4);
+        const int n_order = (int)order.size();
+        {
+            // the first TOP_ORDER inner nodes breadth-first from the root, the others in their
+            // depth-first order; the links are renumbered (the tree itself is unchanged)
+            const int ntop = std::min(n_knodes, TOP_ORDER);
+            std::vector<int> bfs;
+            std::vector<char> top(n_knodes, 0);
+            bfs.reserve(ntop);
+            bfs.push_back(0);
+            top[0] = 1;
+            for (size_t h = 0; h < bfs.size() && (int)bfs.size() < ntop; ++h) {
+                int link[2];
+                memcpy(&link[0], &knodes[4 * (size_t)bfs[h] + 3].x, 4);
+                memcpy(&link[1], &knodes[4 * (size_t)bfs[h] + 3].y, 4);
+                for (int c = 0; c < 2; ++c)
+                    if (link[c] >= 0 && (int)bfs.size() < ntop) {
+                        bfs.push_back(link[c]);
+                        top[link[c]] = 1;
+                    }
+            }
+            std::vector<int> nid(n_knodes);
+            int k = 0;
+            for (int n : bfs) nid[n] = k++;
+            for (int n = 0; n < n_knodes; ++n)
+                if (!top[n]) nid[n] = k++;
+            std::vector<float4> re(knodes.size());
+            for (int n = 0; n < n_knodes; ++n) {
+                float4 *o = &re[4 * (size_t)nid[n]];
+                for (int j = 0; j < 4; ++j) o[j] = knodes[4 * (size_t)n + j];
+                int link[2];
+                memcpy(&link[0], &o[3].x, 4);
+                memcpy(&link[1], &o[3].y, 4);
+                for (int c = 0; c < 2; ++c)
+                    if (link[c] >= 0) link[c] = nid[link[c]];
+                memcpy(&o[3].x, &link[0], 4);
+                memcpy(&o[3].y, &link[1], 4);
+            }
+            knodes.swap(re);
+        }
+        // triangle records
+        std::vector<float4> &tri4 = T.tri4;
+        tri4.assign(3 * (size_t)std::max(n_order, 1), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        for (int i = 0; i < n_order; ++i) {
+            int t = order[i];
+            const float *p0 = d->verts + 3 * d->tris[3 * t], *p1 = d->verts + 3 * d->tris[3 * t + 1],
+                        *p2 = d->verts + 3 * d->tris[3 * t + 2];
+            float idf;
+            memcpy(&idf, &t, 4);
+            // barycentric slack of the float test on incoherent rays: a band of 1e-6 x the scene's
+            // largest coordinate (a few float ulps of a hit point) across the triangle's shortest
+            // altitude, at most 2e-5
+            double a[3] = {(double)p1[0] - p0[0], (double)p1[1] - p0[1], (double)p1[2] - p0[2]};
+            double b[3] = {(double)p2[0] - p0[0], (double)p2[1] - p0[1], (double)p2[2] - p0[2]};
+            double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            double area2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            double c3[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            double lmax = sqrt(std::max({a[0] * a[0] + a[1] * a[1] + a[2] * a[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2],
+                                         c3[0] * c3[0] + c3[1] * c3[1] + c3[2] * c3[2]}));
+            double hmin = lmax > 0.0 ? area2 / lmax : 0.0;
+            float slack = hmin > 0.0 ? (float)std::min(2e-5, 1e-6 * (double)max_abs / hmin) : 2e-5f;
+            tri4[3 * i] = make_float4(p0[0], p0[1], p0[2], idf);
+            tri4[3 * i + 1] = make_float4(p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2], slack);
+            tri4[3 * i + 2] = make_float4(p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2], 0.0f);
+        }
+        T.n_nodes = n_knodes;
+        T.n_tri4 = n_order;
+        T.depth = B.max_depth_seen;
+    };
+    // the tree for rays in every direction, and one for the pixels' first rays, which leave the
+    // hologram plane along +z inside a cone of a few degrees (the faces across z weighted 5:1)
+    Tree tree, tree_p;
+    {
+        const double w_all[3] = {1.0, 1.0, 1.0};
+        make_tree(w_all, tree);
+        const double w_z[3] = {HPT_PRIMARY_SIDE_W, HPT_PRIMARY_SIDE_W, 1.0};
+        make_tree(w_z, tree_p);
     }
     std::vector<double> ref64((size_t)nt * REF_N, 0.0);
     std::vector<float2> refdf((size_t)nt * REF_N);
@@ -758,8 +787,10 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
         off += (bytes + 255) & ~(size_t)255;
         return o;
     };
-    size_t o_nodes = add(knodes.data(), knodes.size() * sizeof(float4));
-    size_t o_tri4 = add(tri4.data(), tri4.size() * sizeof(float4));
+    size_t o_nodes = add(tree.knodes.data(), tree.knodes.size() * sizeof(float4));
+    size_t o_tri4 = add(tree.tri4.data(), tree.tri4.size() * sizeof(float4));
+    size_t o_nodes_p = add(tree_p.knodes.data(), tree_p.knodes.size() * sizeof(float4));
+    size_t o_tri4_p = add(tree_p.tri4.data(), tree_p.tri4.size() * sizeof(float4));
     size_t o_r64 = add(ref64.data(), ref64.size() * sizeof(double));
     size_t o_rdf = add(refdf.data(), refdf.size() * sizeof(float2));
     size_t o_attr = add(attr.data(), attr.size() * sizeof(uint4));
@@ -793,6 +824,8 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     DevScene &s = rec->dev;
     s.nodes = (const float4 *)(base + o_nodes);
     s.tri4 = (const float4 *)(base + o_tri4);
+    s.nodes_p = (const float4 *)(base + o_nodes_p);
+    s.tri4_p = (const float4 *)(base + o_tri4_p);
     s.ref64 = (const double *)(base + o_r64);
     s.refdf = (const float2 *)(base + o_rdf);
     s.tri_attr = (const uint4 *)(base + o_attr);
@@ -809,13 +842,16 @@ extern "C" hpt_status hpt_scene_upload(hpt_ctx *ctx, const hpt_scene_desc *d, ui
     for (int c = 0; c < 3; ++c) { s.cache_bmin[c] = d->cache_bmin[c]; s.cache_bmax[c] = d->cache_bmax[c]; }
     s.cache_res = d->cache_res;
     s.n_tris = nt;
-    s.n_tri4 = n_order;
-    s.n_nodes = n_knodes;
-    s.bvh_depth = B.max_depth_seen;
+    s.n_tri4 = tree.n_tri4;
+    s.n_nodes = tree.n_nodes;
+    s.bvh_depth = tree.depth;
+    s.n_tri4_p = tree_p.n_tri4;
+    s.n_nodes_p = tree_p.n_nodes;
+    s.bvh_depth_p = tree_p.depth;
     s.n_lights = d->nl;
     s.n_points = d->np;
-    rec->n_nodes = n_knodes;
-    rec->depth = B.max_depth_seen;
+    rec->n_nodes = tree.n_nodes;
+    rec->depth = tree.depth;
     std::lock_guard<std::mutex> lk(ctx->mu);
     uint64_t id = ctx->next_scene++;
     ctx->scenes[id] = std::move(rec);
@@ -1138,7 +1174,7 @@ static hpt_status enqueue_waves(hpt_ctx *ctx, const DevJob *jobs, int n, int pre
             g.path_offset = wd.n_paths;
             wd.n_paths += take * spp;
             wd.n_items += take;
-            wd.stack_n = std::max(wd.stack_n, stack_entries(jobs[j].sc.bvh_depth));
+            wd.stack_n = std::max(wd.stack_n, scene_stack_entries(jobs[j].sc));
             max_depth = std::max(max_depth, jobs[j].max_depth);
             c += take;
         }
@@ -1961,7 +1997,7 @@ static void sched_loop(hpt_ctx *ctx)
                         g.path_offset = wd.n_paths;
                         wd.n_paths += pk.second * r.job.spp;
                         wd.n_items += pk.second;
-                        wd.stack_n = std::max(wd.stack_n, stack_entries(r.job.sc.bvh_depth));
+                        wd.stack_n = std::max(wd.stack_n, scene_stack_entries(r.job.sc));
                         max_depth = std::max(max_depth, r.job.max_depth);
                     }
                     // this wave's lane: path state, scratch and stream of its own

@@ -68,6 +68,10 @@ struct DevScene {
     const float4 *nodes;      // 4 float4 per BVH2 node (child boxes + child links)
     int bvh_depth;            // inner levels above the deepest leaf: traversal stack entries needed
     const float4 *tri4;       // 3 float4 per triangle in leaf order: (v0, id), e1, e2
+    // a second tree of the same triangles for the pixels' first rays (along +z of the hologram
+    // plane, within the diffraction cone), with its own leaf-order records
+    const float4 *nodes_p, *tri4_p;
+    int n_nodes_p, n_tri4_p, bvh_depth_p;
     const double *ref64;      // [nt][REF_N]
     const float2 *refdf;      // [nt][REF_N] (hi, lo)
     const uint4 *tri_attr;    // [nt] vertex indices i0, i1, i2, material
@@ -165,6 +169,8 @@ struct PathBufs {
 // traversal stack entries per thread for a BVH of the given depth (inner levels above the
 // deepest leaf): a near-first traversal holds at most one entry per level; one spare
 inline int stack_entries(int bvh_depth) { return bvh_depth + 1 < 2 ? 2 : (bvh_depth + 1 > TSTACK ? TSTACK : bvh_depth + 1); }
+// stack entries for the deeper of a scene's two trees
+inline int scene_stack_entries(const DevScene &s) { return stack_entries(s.bvh_depth > s.bvh_depth_p ? s.bvh_depth : s.bvh_depth_p); }
 
 // device-side scratch of one launch slot
 struct SlotScratch {

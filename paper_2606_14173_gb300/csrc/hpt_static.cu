@@ -192,7 +192,7 @@ extern "C" hpt_status hpt_trace_fixed_scratch(hpt_ctx *ctx, uint64_t scene_id, c
         wd.seg[0].path_offset = 0;
         wd.n_paths = take * J.spp;
         wd.n_items = take;
-        wd.stack_n = stack_entries(J.sc.bvh_depth);
+        wd.stack_n = scene_stack_entries(J.sc);
         FS_TRY(cudaMemsetAsync(L.scr->qcount, 0, sizeof(int) * 3 * (n_iter + 1), s));
         FS_TRY(wave_gen(prec, L.table, wd, L.pb, L.scr, s));
         for (int it = 0; it < n_iter; ++it) {

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK, COH ? HPT_TRACE_MINB : HPT_TRACE_
             pb.hit[p] = make_float4(h.t, h.u, h.v, __int_as_float(h.tri));
         } else if constexpr (COH) {
             traverse<STATS, TRACE_BLOCK>(sc, xyz(o4), xyz(d4), 1e30f, skip, 0.0f, true, false, h, cand, stk, slimit,
-                                         status, cnt);
+                                         status, cnt, it == 0);
             int tri = h.tri;
             if (cand.n > 0) {
                 // the float test was within its error band: decide among the candidates (and the
