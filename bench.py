@@ -48,16 +48,16 @@ ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 FLOP_PER = {"box_tests": 20, "tri_tests": 30, "refines": 400, "vertex": 120, "hologram": 25}
 # DRAM bytes (read + write) per k_trace launch: the average over every launch of both trace
 # kernels in one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 1920x270 band
-# of the 30-sphere scene with 2,097,152-path waves, scaled by 4.0 to the 8,388,608-path waves of
-# the headline frame (the traffic is per ray), copied here: the bench cannot read hardware
-# counters itself.  None whenever k_trace changed since that capture.
+# of the 30-sphere scene with 2,097,152-path waves (the first 120 launches), scaled by 4.0 to the
+# 8,388,608-path waves of the headline frame (the traffic is per ray), copied here: the bench
+# cannot read hardware counters itself.  None whenever k_trace changed since that capture.
 TRACE_DRAM_BYTES_PER_LAUNCH = 138e6
 # Issue counters of the two trace kernels from one ncu --set full capture each on the same band
 # (coherent rays at iteration 0, incoherent and shadow rays at iteration 1), copied here for the
 # same reason: threads active per issued warp instruction (smsp__thread_inst_executed_per_inst_
 # executed / 32) and issue activity (smsp__issue_active).  None whenever k_trace changed since.
-TRACE_ISSUE = {"simt_efficiency": {"coherent": 12.42 / 32, "incoherent_shadow": 13.44 / 32},
-               "issue_active": {"coherent": 0.615, "incoherent_shadow": 0.662}}
+TRACE_ISSUE = {"simt_efficiency": {"coherent": 12.24 / 32, "incoherent_shadow": 13.44 / 32},
+               "issue_active": {"coherent": 0.619, "incoherent_shadow": 0.662}}
 
 
 # name -> (description, scene factory, render factory)
