@@ -91,3 +91,42 @@ def test_all_rejected_gives_counts_only(bench):
     hpt = types.SimpleNamespace(HptError=_Err, PREC_DF32=1)
     res = bench.serve_owned(AllBusy(), hpt, _requests(3), 1e6, 0)
     assert res == {"requests": 3, "rejected": 3, "offered_rate_per_s": 1e6}
+
+
+class _DoneProc:
+    """Stands in for the nvidia-smi process once its samples are in."""
+
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _clock_rows(samples):
+    # (time, [index, clocks.sm, clocks.max.sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap])
+    return [(t, ["0", str(sm), "2070", "900.0", "0x0", hw, "Not Active", "Not Active", pc]) for t, sm, hw, pc in samples]
+
+
+def test_clock_sampler_keeps_the_timed_window_and_reports_reasons(bench):
+    """The bench's clock record: only samples inside the timed window count; the median SM clock,
+    the maximum clock and every throttle reason seen active inside the window are reported."""
+    clk = bench.ClockSampler(0)
+    clk.proc = _DoneProc()
+    clk.rows = _clock_rows([(0.0, 345, "Not Active", "Not Active"),      # start-up, outside the window
+                            (1.0, 2070, "Not Active", "Not Active"),
+                            (1.2, 2055, "Not Active", "Active"),
+                            (1.4, 2070, "Not Active", "Not Active"),
+                            (9.0, 900, "Active", "Not Active")])         # after the window
+    clk.window(0.9, 1.5)
+    rec = clk.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    clk.rows.append((1.3, ["0", "1500", "2070", "800", "0x8", "Active", "Not Active", "Not Active", "Not Active"]))
+    clk.rows.append((1.35, ["0", "garbled"]))                             # a broken line is skipped
+    rec = clk.stop()
+    assert rec["reasons"] == ["hw_slowdown", "sw_power_cap"] and rec["samples"] == 4
+
+
+def test_clock_sampler_without_nvidia_smi(bench):
+    clk = bench.ClockSampler(0)
+    assert clk.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
